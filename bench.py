@@ -1,0 +1,381 @@
+"""Benchmark of the reproducible Jacobi-PCG hot path on one GB300.
+
+Headline: PCG iterations per second of the exblas variant on the 27-point
+3D Poisson operator on a 256^3 grid (n = 16,777,216, nnz = 449,455,096,
+FP64 CSR with int32 indices, Jacobi preconditioner, b = A x_true with
+x_true ~ U[-1, 1], x0 = 0, tol 1e-8, at most 5000 iterations).  One step
+is one complete solve (set-up plus every iteration until convergence);
+value = iterations of the K timed solves / their device time.
+
+Also reported on the same JSON line: the plain (non-reproducible,
+tree-reduction) GPU PCG and the overhead ratio, the fpe variant's rate, the
+exact dot's GB/s on 2^28-element U[-1, 1] pairs, the roofline of the
+dominant kernel (pass A: SpMV + <d, w>), an end-to-end number through the
+host-buffer C ABI, and the CPU oracle timed on the host cores.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank solves its own copy of the system (the solve does
+not shard across GPUs here: replicas only); value sums all ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+METRIC = "PCG iters/s & overhead vs plain GPU PCG; exact-dot GB/s vs HBM peak (bit-exact)"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--side", type=int, default=256, help="grid side of the 27-point Poisson workload")
+    ap.add_argument("--max-iter", type=int, default=5000)
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip the plain/fpe/dot/e2e side measurements")
+    return ap.parse_args()
+
+
+def hbm_peak():
+    try:
+        with open(PEAKS_FILE) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def workload(side):
+    A = synth.poisson27(side)
+    xt = synth.poisson_rhs_xtrue(A.n, synth.BASE_SEED + 2)
+    return A, xt
+
+
+def pass_a_bytes(n, nnz):
+    """Algorithmic bytes of one pass-A launch: CSR stream, d read once, w written once."""
+    return 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n
+
+
+def iter_bytes(n, nnz):
+    """Algorithmic bytes of one PCG iteration (three passes, z recomputed)."""
+    return 12 * nnz + 4 * (n + 1) + 88 * n
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+
+    FIELDS = "clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.out = None
+
+    def start(self):
+        try:
+            self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-i", str(self.index), "-lms", "200"], stdout=self.out,
+                                         stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        self.out.seek(0)
+        rows = [ln.strip().split(", ") for ln in self.out.read().splitlines() if ln.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for nm, v in zip(names, r[3:7]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def cpu_oracle_rate(A, b, iters, tol):
+    """The oracle as it stands, on all host cores: iterations per second of
+    its PCG loop (set-up excluded) over a bounded number of iterations."""
+    import oracle
+    nt = oracle.default_threads()
+    r = oracle.pcg(A, b, variant=oracle.EXACT, tol=tol, max_iter=iters, nthreads=nt)
+    return r["iterations"] / max(r["loop_seconds"], 1e-9), r["iterations"], r["loop_seconds"], nt
+
+
+def reference_arm(args, rank, world):
+    """--impl reference: the CPU oracle, timed on the host cores (rank 0 only)."""
+    if rank != 0:
+        return
+    import oracle
+    A, xt = workload(args.side)
+    b = oracle.spmv(A, xt, nthreads=oracle.default_threads())
+    per_step = 2
+    for _ in range(args.warmup):
+        cpu_oracle_rate(A, b, 1, args.tol)
+    its, secs = 0, 0.0
+    nt = 1
+    for _ in range(args.steps):
+        _, it, s, nt = cpu_oracle_rate(A, b, per_step, args.tol)
+        its += it
+        secs += s
+    v = its / secs
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"poisson27_{args.side}", "n": A.n, "nnz": A.nnz, "tol": args.tol,
+                       "step": f"{per_step} PCG iterations of the oracle (set-up excluded from the time)"},
+            "cpu_baseline": {"value": v, "unit": "iters/s", "cores": nt, "kind": "oracle",
+                             "sample": f"{args.steps} x {per_step} iterations of the exact-dot PCG"},
+            "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def gpu_arm(args, rank, world, local_rank):
+    import torch
+
+    import paper_2005_07282_gb300 as P
+    from paper_2005_07282_gb300 import build as B
+
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    B.build()
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+    stream = torch.cuda.current_stream()
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---- inputs (host CSR in pinned memory for the end-to-end leg)
+    A, xt = workload(args.side)
+    n, nnz = A.n, A.nnz
+    M = P.Matrix.from_csr(A)
+    d_xt = torch.from_numpy(xt).to(dev)
+    d_b = M.spmv(d_xt)
+    torch.cuda.synchronize()
+    x = torch.zeros(n, dtype=torch.float64, device=dev)
+    opts = dict(tol=args.tol, max_iter=args.max_iter)
+
+    def solve(variant, **kw):
+        x.zero_()
+        return M.solve(d_b, x, variant=variant, **{**opts, **kw})
+
+    # ---- warm-up (builds and caches the graphs)
+    for _ in range(args.warmup):
+        r = solve("exblas")
+    iters_per_solve = r["iterations"]
+    status = r["status"]
+
+    # ---- timed region: K full exblas solves
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    total_iters = 0
+    for _ in range(args.steps):
+        r = solve("exblas")
+        total_iters += r["iterations"]
+    e1.record(stream)
+    barrier()
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ms_max = max_over_ranks(ms)
+    all_iters = sum_over_ranks(total_iters)
+    value = all_iters / (ms_max / 1e3)
+    launches = args.steps * (4 + 3 * iters_per_solve)
+
+    extras = {}
+    cpu = None
+    roof = None
+    e2e = None
+    if not args.no_extras:
+        # plain GPU PCG (tree-reduction dots): the overhead baseline
+        rp = solve("plain")
+        torch.cuda.synchronize()
+        e0.record(stream)
+        pit = 0
+        for _ in range(args.steps):
+            rp = solve("plain")
+            pit += rp["iterations"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain_rate = pit / (pms / 1e3)
+        extras["plain_iters_per_s"] = plain_rate
+        extras["plain_iterations"] = rp["iterations"]
+        extras["overhead_vs_plain"] = plain_rate / (total_iters / (ms / 1e3))
+        # fpe variant (FPE8 with early exit; FP64-pipe bound on this GPU), bounded iterations
+        fit = min(100, iters_per_solve)
+        solve("fpe", max_iter=5)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        rf = solve("fpe", max_iter=fit)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        extras["fpe_iters_per_s"] = rf["iterations"] / (e0.elapsed_time(e1) / 1e3)
+        extras["fpe_sample_iterations"] = rf["iterations"]
+        # per-pass event timing (same kernels launched one by one), bounded iterations
+        x.zero_()
+        prof = M.solve_profiled(d_b, x, variant="exblas", tol=args.tol, max_iter=min(60, iters_per_solve))
+        la = prof["launches"]["A"]
+        a_ms = prof["pass_ms"]["A"] / max(la, 1)
+        b_ms = prof["pass_ms"]["B"] / max(la, 1)
+        c_ms = prof["pass_ms"]["C"] / max(la, 1)
+        peak, peak_kind = hbm_peak()
+        ach = pass_a_bytes(n, nnz) / (a_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "traffic": None, "kernel": "k_pass_a (SpMV + <d,w> exact deposit)",
+                "peak_kind": f"{peak_kind} copy bandwidth",
+                "algorithmic_bytes_per_launch": pass_a_bytes(n, nnz), "avg_launch_ms": a_ms}
+        extras["pass_ms"] = {"A": a_ms, "B": b_ms, "C": c_ms}
+        it_ms = ms / max(total_iters, 1)
+        extras["iteration_roofline"] = {"bytes_per_iter": iter_bytes(n, nnz), "ms_per_iter": it_ms,
+                                        "achieved_gbs": iter_bytes(n, nnz) / (it_ms * 1e-3) / 1e9,
+                                        "frac": iter_bytes(n, nnz) / (it_ms * 1e-3) / 1e9 / peak}
+        # exact dot GB/s: 2^28 U[-1,1] pairs (a 2^24 draw tiled 16x in HBM)
+        nd = 1 << 28
+        base_a, base_b = synth.dot_family_a(1 << 24, synth.BASE_SEED + 1)
+        da = torch.from_numpy(base_a).to(dev).repeat(16)
+        db = torch.from_numpy(base_b).to(dev).repeat(16)
+        out = torch.empty((), dtype=torch.float64, device=dev)
+        for _ in range(3):
+            P.dot_exact(da, db, out=out)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        reps = 10
+        for _ in range(reps):
+            P.dot_exact(da, db, out=out)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        dms = e0.elapsed_time(e1) / reps
+        gbs = 16 * nd / (dms * 1e-3) / 1e9
+        e0.record(stream)
+        for _ in range(reps):
+            P.dot_plain(da, db)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pgbs = 16 * nd / (e0.elapsed_time(e1) / reps * 1e-3) / 1e9
+        extras["exact_dot"] = {"n": nd, "gbs": gbs, "frac": gbs / peak, "ms": dms, "plain_dot_gbs": pgbs,
+                               "inputs": "U[-1,1] pairs, 2^24 draw tiled 16x (4.3 GB, larger than L2)"}
+        del da, db
+        # end to end through the host-buffer ABI: create from pinned host CSR, solve_host, destroy
+        h_rowptr = torch.from_numpy(A.rowptr).pin_memory()
+        h_col = torch.from_numpy(A.col).pin_memory()
+        h_val = torch.from_numpy(A.val).pin_memory()
+        h_b = d_b.cpu().pin_memory()
+        h_x = torch.zeros(n, dtype=torch.float64).pin_memory()
+        e2e_steps = max(1, min(args.steps, 2))
+        t0 = time.perf_counter()
+        eit = 0
+        for _ in range(e2e_steps):
+            M2 = P.Matrix(h_rowptr.numpy(), h_col.numpy(), h_val.numpy(), n=n)
+            h_x.zero_()
+            re = M2.solve_host(h_b.numpy(), h_x.numpy(), variant="exblas", **opts)
+            eit += re["iterations"]
+            M2.close()
+        torch.cuda.synchronize()
+        et = time.perf_counter() - t0
+        e2e = {"value": sum_over_ranks(eit) / max_over_ranks(et), "unit": "iters/s",
+               "h2d_bytes_per_step": int(12 * nnz + 4 * (n + 1) + 16 * n), "d2h_bytes_per_step": int(8 * n + 64),
+               "path": "rpcg_create(host CSR) + rpcg_solve_host + rpcg_destroy"}
+        del M2
+        if rank == 0 and not args.no_cpu_baseline:
+            import oracle
+            b_host = d_b.cpu().numpy()
+            crate, cit, csec, cores = cpu_oracle_rate(A, b_host, 3, args.tol)
+            cpu = {"value": crate, "unit": "iters/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{cit} exact-dot PCG iterations of the same system ({csec:.1f} s, set-up excluded)"}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": f"poisson27_{args.side} exblas", "n": n, "nnz": nnz, "tol": args.tol,
+                           "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
+                           "solve_status": status, "step": "one complete solve from x0 = 0",
+                           "l2": "inputs larger than L2 (CSR 5.46 GB streamed every iteration)",
+                           "parallelism": f"replicas x{world}"},
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, **extras}
+        print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        reference_arm(args, rank, world)
+        return
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        torch.cuda.set_device(local_rank)
+        dist.init_process_group("nccl")
+    try:
+        gpu_arm(args, rank, world, local_rank)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,211 @@
+/*
+ * rpcg.h -- C ABI of the reproducible Jacobi-preconditioned CG library for
+ * one NVIDIA GB300 (sm_103a).
+ *
+ * The method is the reproducible PCG of Iakymchuk, Barreda, Graillat,
+ * Aliaga and Quintana-Orti ("Reproducibility of Parallel Preconditioned
+ * Conjugate Gradient in Hybrid Programming Environments"): the PCG loop of
+ * Fig. 1 with S8 moved next to S6 (Fig. 2), a Jacobi preconditioner applied
+ * as an elementwise multiply by the inverse diagonal (Sec. 3.1, Sec. 4.3),
+ * SpMV rows and AXPY updates written with explicit fma (Sec. 4.3), and the
+ * three dot products made reproducible either with an ExBLAS-style long
+ * accumulator (Sec. 2.1, Sec. 4.1) or with floating-point expansions
+ * (Sec. 4.2, Algs. 1-4).
+ *
+ * Conventions for every entry point:
+ *   - All arithmetic is IEEE binary64, round to nearest even.
+ *   - "device" pointers are CUDA device (or managed) memory on the current
+ *     device; "host" pointers are ordinary host memory.  Vectors are dense,
+ *     contiguous, unit stride.  CSR matrices use int32 row pointers
+ *     (n + 1 entries, rowptr[0] = 0, non-decreasing) and int32 column
+ *     indices, float64 values; columns may be in any order inside a row,
+ *     and the SpMV sums each row in storage order.
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *     stream).  Work is enqueued on it.  Entry points that return values
+ *     into host memory synchronise that stream before returning.
+ *   - Nothing aborts or throws across the ABI.  Every call returns an
+ *     rpcg_status; rpcg_last_error() gives a human-readable message for the
+ *     last failing call on the calling host thread.
+ *   - A matrix handle may be used by one host thread at a time.
+ */
+#ifndef RPCG_H
+#define RPCG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Status codes.  Non-negative values are solver outcomes, negative values
+ * are errors. */
+typedef enum {
+    RPCG_OK = 0,
+    RPCG_NOT_CONVERGED = 1,  /* max_iter reached with relres >= tol */
+    RPCG_FPE_INEXACT = 2,    /* fpe variant with fpe_strict = 1: an expansion lost bits (Sec. 4.3, warning) */
+    RPCG_ERR_INVALID = -1,   /* bad argument */
+    RPCG_ERR_NOT_SPD = -2,   /* missing or non-positive diagonal, <d,w> <= 0, or beta <= 0 with tau > 0 */
+    RPCG_ERR_NONFINITE = -3, /* NaN or Inf met in a dot product or the diagonal */
+    RPCG_ERR_OOM = -4,       /* device allocation failed, or a budget was exceeded */
+    RPCG_ERR_CUDA = -5,      /* a CUDA runtime call failed */
+    RPCG_ERR_TIMEOUT = -6    /* a bounded wait ran out (server wait) */
+} rpcg_status;
+
+/* Dot-product variants of the solver (Sec. 4). */
+typedef enum {
+    RPCG_PLAIN = 0,  /* ordinary FP64 dots with a fixed tree reduction (not reproducible across launch shapes) */
+    RPCG_EXBLAS = 1, /* exact dot: long accumulator of 64-bit digits, one final rounding (Sec. 4.1) */
+    RPCG_FPE = 2     /* floating-point-expansion dot with an exactness flag (Sec. 4.2) */
+} rpcg_variant;
+
+typedef struct rpcg_matrix_s *rpcg_matrix_t;
+typedef struct rpcg_server_s *rpcg_server_t;
+
+/* Solver options.  rpcg_opts_default() fills the defaults. */
+typedef struct {
+    double tol;         /* stop when RN(sqrt(tau) / ||b||) < tol (default 1e-8) */
+    int32_t max_iter;   /* loop bodies at most (default 1000) */
+    int32_t fpe_size;   /* terms per expansion p, 1..8 (default 8, Sec. 4.2) */
+    int32_t fpe_strict; /* fpe variant: 0 = recompute an inexact dot exactly (default), 1 = report RPCG_FPE_INEXACT */
+    int32_t block;      /* threads per CTA of the streaming passes: 0 = auto, else 128, 256 or 512 */
+    int32_t grid;       /* CTAs of the streaming passes: 0 = auto, else 1 .. 4096 */
+    int32_t reserved;
+    double *history;    /* optional device array of max_iter + 1 doubles: relres at every loop test */
+} rpcg_opts;
+
+/* Outcome of a solve. */
+typedef struct {
+    int32_t iterations;        /* loop bodies executed */
+    int32_t status;            /* rpcg_status of this solve */
+    double relres;             /* RN(sqrt(tau) / ||b||) at the last loop test */
+    double tau;                /* <r, r> at the last loop test */
+    int32_t fpe_inexact_count; /* fpe variant: dots whose expansion lost bits */
+    int32_t reserved;
+} rpcg_result;
+
+/* Fill `o` with the defaults listed in rpcg_opts. */
+void rpcg_opts_default(rpcg_opts *o);
+
+/* Text for a status code (static storage). */
+const char *rpcg_status_string(int32_t status);
+
+/* Message of the last failing call on this host thread ("" if none). */
+const char *rpcg_last_error(void);
+
+/*
+ * rpcg_create -- build a matrix handle from CSR (Sec. 3.1: A is sparse SPD
+ * with n rows and nnz nonzeros; the handle also computes the Jacobi
+ * preconditioner's inverse diagonal on first use).
+ *   A_out     receives the handle.
+ *   n, nnz    rows and nonzeros, 0 <= n < 2^31, 0 <= nnz < 2^31.
+ *   rowptr, col, val   CSR arrays (n + 1, nnz, nnz entries).
+ *   ptr_kind  0 = the three arrays are host pointers, 1 = device pointers.
+ * The handle copies the arrays into device memory it owns (padded for
+ * aligned bulk loads) and allocates the Krylov vectors; the caller's arrays
+ * may be freed as soon as the call returns.  Row pointers are validated
+ * (monotone, in range); column indices are checked to lie in [0, n).
+ * Errors: RPCG_ERR_INVALID (bad sizes or CSR), RPCG_ERR_OOM, RPCG_ERR_CUDA.
+ */
+rpcg_status rpcg_create(rpcg_matrix_t *A_out, int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
+                        const double *val, int32_t ptr_kind, void *stream);
+
+/* Release a handle and all device memory it owns (synchronises its work). */
+rpcg_status rpcg_destroy(rpcg_matrix_t A);
+
+/* Rows and nonzeros of a handle. */
+rpcg_status rpcg_matrix_info(rpcg_matrix_t A, int32_t *n, int32_t *nnz);
+
+/*
+ * rpcg_spmv -- y = A x (S1 of Fig. 1), each row summed left to right in
+ * storage order as acc = fma(val_k, x_col_k, acc) from acc = +0 (Sec. 4.3).
+ * x, y: device arrays of n doubles (must not overlap).  Asynchronous.
+ */
+rpcg_status rpcg_spmv(rpcg_matrix_t A, const double *x, double *y, void *stream);
+
+/*
+ * rpcg_dot_exact -- out = RN(sum_i a_i * b_i) with the sum taken exactly
+ * (Sec. 2.1 and Sec. 4.1: every product is kept exactly in a long
+ * accumulator of 64-bit digits and rounded once, to nearest even).
+ *   n       0 <= n <= 2^30.
+ *   a, b    device arrays of n doubles.
+ *   out     device pointer to one double.
+ * An exactly zero sum gives +0; a non-zero sum that rounds to zero keeps
+ * its sign; |sum| >= 2^1024 (1 - 2^-54) gives +-inf; any NaN or Inf input
+ * gives NaN.  The result does not depend on the launch shape, the stream
+ * or the order of the elements.  Scratch memory is taken from the
+ * stream-ordered pool (cudaMallocAsync).  Asynchronous.
+ */
+rpcg_status rpcg_dot_exact(int64_t n, const double *a, const double *b, double *out, void *stream);
+
+/*
+ * rpcg_dot_fpe -- FPE dot of Sec. 4.2 / Listing 2: each thread keeps a
+ * result expansion and an error expansion of p terms (Alg. 4 with the early
+ * exit, fed by Alg. 2's product and error), the expansions are merged with
+ * Alg. 3 in a fixed tree, and the merged expansion is rounded correctly
+ * (the value NearSum returns).
+ *   p       terms per expansion, 1..8.
+ *   out     device pointer to one double.
+ *   exact   device pointer to one int32: 1 if no bits were lost (then *out
+ *           equals rpcg_dot_exact's value), 0 if an expansion carried a
+ *           value out of its last term, a product fell below 2^-969, or a
+ *           term became non-finite.
+ * Asynchronous.
+ */
+rpcg_status rpcg_dot_fpe(int64_t n, const double *a, const double *b, int32_t p, double *out, int32_t *exact,
+                         void *stream);
+
+/*
+ * rpcg_dot_plain -- ordinary FP64 dot (fma per element per thread, fixed
+ * shuffle/shared-memory tree, then a fixed tree over CTA partials).  The
+ * non-reproducible baseline of the paper's "Regular" PCG (Sec. 5.2).
+ * out: device pointer to one double.  Asynchronous.
+ */
+rpcg_status rpcg_dot_plain(int64_t n, const double *a, const double *b, double *out, void *stream);
+
+/*
+ * rpcg_solve -- Jacobi-PCG (Fig. 1, S8 next to S6 as in Fig. 2) on A.
+ *   b        device array, n doubles (right-hand side).
+ *   x        device array, n doubles: in = x0, out = the final iterate.
+ *   v        dot variant (rpcg_variant).
+ *   o        options (NULL = defaults).
+ *   res      host pointer, receives the outcome (the stream is synchronised).
+ * Steps per iteration: w = A d; rho = RN(beta / <d,w>); x = fma(rho, d, x);
+ * r = fma(-rho, w, r); z = RN(inv .* r); beta' = beta; beta = <z,r>;
+ * tau = <r,r>; d = fma(RN(beta / beta'), d, z).  Set-up: inv = RN(1/diag),
+ * r0 = RN(b - A x0), z0 = inv .* r0, d0 = z0, beta0 = <z0,r0>,
+ * tau0 = <r0,r0>, ||b|| = RN(sqrt(<b,b>)).  The loop runs on the device
+ * (a CUDA graph with a conditional while node) while relres >= tol and
+ * iterations < max_iter.  With RPCG_EXBLAS, and RPCG_FPE with
+ * fpe_strict = 0, every iterate, residual and the iteration count are
+ * bit-identical for every launch shape.  b = 0 gives x = 0, 0 iterations.
+ * Returns res->status.
+ */
+rpcg_status rpcg_solve(rpcg_matrix_t A, const double *b, double *x, int32_t v, const rpcg_opts *o, rpcg_result *res,
+                       void *stream);
+
+/*
+ * rpcg_solve_profiled -- rpcg_solve with the same kernels launched one by
+ * one from the host instead of the graph, and CUDA events recorded on
+ * `stream` around each pass.  Results are bit-identical to rpcg_solve.
+ *   pass_ms   host array of 4 floats: total milliseconds spent in the
+ *             set-up, pass A (S1 + S2), pass B (S3-S6, S8), pass C (S7).
+ *   launches  optional host array of 4 int32: launches of each.
+ * It synchronises the stream once per iteration: a measurement tool.
+ */
+rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double *b, double *x, int32_t v, const rpcg_opts *o,
+                                rpcg_result *res, float *pass_ms, int32_t *launches, void *stream);
+
+/*
+ * rpcg_solve_host -- rpcg_solve with b and x in host memory: b and x0 are
+ * copied to device buffers the handle owns, the solve runs, and x is
+ * copied back.  Same semantics and result as rpcg_solve.
+ */
+rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double *b_host, double *x_host, int32_t v, const rpcg_opts *o,
+                            rpcg_result *res, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPCG_H */

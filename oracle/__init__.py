@@ -57,6 +57,8 @@ def _load():
         L.oracle_dot_fpe.argtypes = [i64, P, P, ctypes.c_int, ctypes.c_int, P]
         L.oracle_spmv.restype = None
         L.oracle_spmv.argtypes = [i32, P, P, P, P, P, ctypes.c_int]
+        L.oracle_pcg_loop_seconds.restype = d
+        L.oracle_pcg_loop_seconds.argtypes = []
         L.oracle_pcg.restype = ctypes.c_int
         L.oracle_pcg.argtypes = [i32, P, P, P, P, P, ctypes.c_int, d, i32, P, P, P, P, ctypes.c_int]
         _lib = L
@@ -149,4 +151,4 @@ def pcg(A, b, x0=None, variant: int = EXACT, tol: float = 1e-8, max_iter: int = 
     st = _load().oracle_pcg(A.n, _ptr(rp), _ptr(cl), _ptr(vl), _ptr(b), _ptr(x), variant, tol, max_iter,
                             _ptr(hist), ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tt), nthreads)
     return dict(x=x, status=st, iterations=it.value, relres=rr.value, tau=tt.value,
-                history=hist[: it.value + 1].copy())
+                history=hist[: it.value + 1].copy(), loop_seconds=_load().oracle_pcg_loop_seconds())

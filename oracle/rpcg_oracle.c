@@ -36,11 +36,13 @@
  * x = fma(rho,d,x); r = fma(-rho,w,r); gamma = RN(beta_new/beta_old);
  * d = fma(gamma,d,z); SpMV accumulator starts at +0.0.
  */
+#define _POSIX_C_SOURCE 199309L
 #include <math.h>
 #include <pthread.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#include <time.h>
 
 /* ------------------------------------------------------------------ */
 /* Status codes (the oracle's own copy of the values the solver reports) */
@@ -421,9 +423,22 @@ static double dot_v(int variant, int64_t n, const double *a, const double *b, in
  * every loop test, history[l] for l = 0 .. iterations.
  * Returns a status code.
  */
+static double now_seconds(void) {
+    struct timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return (double)ts.tv_sec + 1e-9 * (double)ts.tv_nsec;
+}
+
+/* Instrumentation only: wall-clock seconds spent in the iteration loop of
+ * the last oracle_pcg call (excludes the set-up).  Used to time the oracle
+ * as a CPU baseline; it does not influence any result. */
+static double g_loop_seconds = 0.0;
+double oracle_pcg_loop_seconds(void) { return g_loop_seconds; }
+
 int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b, double *x,
                int variant, double tol, int32_t max_iter, double *history, int32_t *iterations, double *relres_out,
                double *tau_out, int nthreads) {
+    g_loop_seconds = 0.0;
     *iterations = 0;
     *relres_out = NAN;
     *tau_out = NAN;
@@ -478,6 +493,7 @@ int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const doubl
     int32_t l = 0;
     double rel = sqrt(tau) / bnorm;
     if (history) history[0] = rel;
+    double t_loop = now_seconds();
     while (rel >= tol && l < max_iter) {
         double beta_old = beta;
         /* S1 */
@@ -516,6 +532,7 @@ int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const doubl
             break;
         }
     }
+    g_loop_seconds = now_seconds() - t_loop;
     *iterations = l;
     *relres_out = rel;
     *tau_out = tau;

@@ -1,0 +1,329 @@
+// Device primitives of the reproducible dot products.
+//
+// Exact dot (Sec. 2.1, Sec. 4.1).  A finite double is +-m 2^e with integer
+// m < 2^53 and e >= -1074, so a product is +-M 2^E with M = m_a m_b < 2^106
+// and E >= -2148.  The long accumulator is a fixed-point integer whose bit 0
+// weighs 2^kE0; it is stored as kNDig signed 64-bit digits, digit k holding
+// a sum of 32-bit chunks of weight 2^(32k + kE0).  A digit only ever
+// receives values below 2^32 in magnitude, so 2^31 deposits fit in its 64
+// bits without a carry (the paper's carry-safe headroom, Sec. 4.3; here
+// 32 headroom bits instead of 12).
+//
+// GB300 has ~1.7 FP64 instructions per clock per SM against ~120 simple
+// integer instructions, so the per-element work of the exact dot runs on
+// the integer pipe: the 106-bit product is formed with 32x32-bit multiplies
+// and added, shifted, into a 224-bit register window (a per-thread long
+// accumulator segment, the role the FPE plays in ExBLAS); products outside
+// the window go to a shared-memory accumulator with 64-bit atomics; the CTA
+// accumulators meet in global memory with 64-bit atomics (exact and
+// order-independent, the single-GPU form of Listing 3's MPI_Reduce); the
+// last CTA normalises the carries and rounds once (Round in Listing 3).
+//
+// FPE dot (Sec. 4.2).  twosum (Alg. 1), twoprod (Alg. 2), Accumulate with
+// early exit (Alg. 4) and fpesum (Alg. 3) in FP64.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace rpcg {
+
+constexpr int kE0 = -2176;            // weight exponent of accumulator bit 0
+constexpr int kNDig = 136;            // 32-bit digits (4352 bits)
+constexpr int kSubLsb = -1074 - kE0;  // bit index of 2^-1074 (1102)
+constexpr int kCopies = 8;            // shared-memory accumulator copies (spread contention)
+constexpr int kWin = 7;               // 32-bit words of the register window
+constexpr int kFpeMax = 8;            // largest expansion size
+
+// ------------------------------------------------------------------ exact products
+
+// |a*b| as five 32-bit words already shifted by the in-digit offset, the
+// digit index q of word 0, the sign as an all-ones mask, and flags.
+struct ExactProd {
+  uint32_t w0, w1, w2, w3, w4;
+  int q;
+  uint32_t neg;
+  bool nz;
+  bool bad;  // a or b is Inf or NaN
+};
+
+__device__ __forceinline__ ExactProd exact_product(double a, double b) {
+  const uint64_t ba = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
+  uint32_t ea = (uint32_t)(ba >> 52) & 0x7ffu, eb = (uint32_t)(bb >> 52) & 0x7ffu;
+  uint64_t ma = ba & 0xFFFFFFFFFFFFFull, mb = bb & 0xFFFFFFFFFFFFFull;
+  ExactProd p;
+  p.bad = (ea == 0x7ffu) | (eb == 0x7ffu);
+  // normal numbers get the hidden bit; subnormals have the exponent of field 1
+  if (ea) ma |= 1ull << 52; else ea = 1;
+  if (eb) mb |= 1ull << 52; else eb = 1;
+  p.nz = (ma != 0) & (mb != 0) & !p.bad;
+  // product LSB weight 2^(ea + eb - 2150); offset from 2^kE0
+  const int o = (int)(ea + eb) - 2150 - kE0;  // 28 .. 4118
+  p.q = o >> 5;
+  const int r = o & 31;
+  const uint64_t lo = ma * mb;
+  const uint64_t hi = __umul64hi(ma, mb);  // < 2^42
+  const uint32_t v0 = (uint32_t)lo, v1 = (uint32_t)(lo >> 32), v2 = (uint32_t)hi, v3 = (uint32_t)(hi >> 32);
+  p.w0 = v0 << r;
+  p.w1 = __funnelshift_l(v0, v1, r);
+  p.w2 = __funnelshift_l(v1, v2, r);
+  p.w3 = __funnelshift_l(v2, v3, r);
+  p.w4 = __funnelshift_l(v3, 0u, r);
+  p.neg = ((ba ^ bb) >> 63) ? 0xffffffffu : 0u;
+  return p;
+}
+
+// signed 64-bit contribution of an unsigned 32-bit chunk under a sign mask
+__device__ __forceinline__ unsigned long long signed_chunk(uint32_t w, uint32_t neg) {
+  const long long v = (long long)w;
+  return (unsigned long long)(neg ? -v : v);
+}
+
+// Deposit a product into a shared-memory accumulator laid out as
+// sacc[digit * kCopies + copy] (64-bit atomics; wrap-around addition of
+// two's-complement values is exact while the true digit sum fits).
+__device__ __forceinline__ void smem_deposit(unsigned long long* sacc, int copy, const ExactProd& p) {
+  unsigned long long* base = sacc + p.q * kCopies + copy;
+  if (p.w0) atomicAdd(base + 0 * kCopies, signed_chunk(p.w0, p.neg));
+  if (p.w1) atomicAdd(base + 1 * kCopies, signed_chunk(p.w1, p.neg));
+  if (p.w2) atomicAdd(base + 2 * kCopies, signed_chunk(p.w2, p.neg));
+  if (p.w3) atomicAdd(base + 3 * kCopies, signed_chunk(p.w3, p.neg));
+  if (p.w4) atomicAdd(base + 4 * kCopies, signed_chunk(p.w4, p.neg));
+}
+
+// Per-thread register window: a 224-bit two's-complement integer W whose
+// word 0 has digit index qb.  Products whose digit index is qb or qb + 1
+// are added with one carry chain; others go to shared memory.  When a
+// larger product arrives the window is flushed and moved up so that it
+// tracks the top of the magnitude range.
+struct Window {
+  uint32_t W[kWin];
+  int qb;  // -1: not anchored yet
+};
+
+__device__ __forceinline__ void window_init(Window& w) {
+#pragma unroll
+  for (int k = 0; k < kWin; k++) w.W[k] = 0;
+  w.qb = -1;
+}
+
+__device__ __forceinline__ void window_flush(Window& w, unsigned long long* sacc, int copy) {
+  if (w.qb < 0) return;
+  unsigned long long* base = sacc + w.qb * kCopies + copy;
+#pragma unroll
+  for (int k = 0; k < kWin - 1; k++) {
+    if (w.W[k]) atomicAdd(base + k * kCopies, (unsigned long long)w.W[k]);
+  }
+  // the top word carries the sign of the whole window
+  if (w.W[kWin - 1]) atomicAdd(base + (kWin - 1) * kCopies, (unsigned long long)(long long)(int)w.W[kWin - 1]);
+#pragma unroll
+  for (int k = 0; k < kWin; k++) w.W[k] = 0;
+}
+
+// W += (neg ? -1 : 1) * (p.w << 32 t), t in {0, 1}: the addend is formed
+// as (chunk XOR mask) with carry-in (mask & 1) -- two's-complement negation
+// folded into one add-with-carry chain.
+__device__ __forceinline__ void window_add(Window& w, const ExactProd& p, bool t1) {
+  const uint32_t m = p.neg;
+  const uint32_t a0 = (t1 ? 0u : p.w0) ^ m;
+  const uint32_t a1 = (t1 ? p.w0 : p.w1) ^ m;
+  const uint32_t a2 = (t1 ? p.w1 : p.w2) ^ m;
+  const uint32_t a3 = (t1 ? p.w2 : p.w3) ^ m;
+  const uint32_t a4 = (t1 ? p.w3 : p.w4) ^ m;
+  const uint32_t a5 = (t1 ? p.w4 : 0u) ^ m;
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "add.cc.u32 t, %7, %7;\n\t"
+      "addc.cc.u32 %0, %0, %8;\n\t"
+      "addc.cc.u32 %1, %1, %9;\n\t"
+      "addc.cc.u32 %2, %2, %10;\n\t"
+      "addc.cc.u32 %3, %3, %11;\n\t"
+      "addc.cc.u32 %4, %4, %12;\n\t"
+      "addc.cc.u32 %5, %5, %13;\n\t"
+      "addc.u32 %6, %6, %7;\n\t"
+      "}"
+      : "+r"(w.W[0]), "+r"(w.W[1]), "+r"(w.W[2]), "+r"(w.W[3]), "+r"(w.W[4]), "+r"(w.W[5]), "+r"(w.W[6])
+      : "r"(m), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5));
+}
+
+__device__ __forceinline__ void exact_deposit(Window& w, unsigned long long* sacc, int copy, const ExactProd& p) {
+  if (!p.nz) return;
+  if (w.qb < 0) {
+    int qb = p.q - 1;
+    w.qb = qb < 0 ? 0 : (qb > kNDig - kWin ? kNDig - kWin : qb);
+  }
+  const int t = p.q - w.qb;
+  if (t == 0 || t == 1) {
+    window_add(w, p, t == 1);
+  } else if (t > 1 && p.q - 1 <= kNDig - kWin) {
+    // a larger product: move the window up to it
+    window_flush(w, sacc, copy);
+    w.qb = p.q - 1;
+    window_add(w, p, true);
+  } else {
+    smem_deposit(sacc, copy, p);
+  }
+}
+
+// Sum the kCopies copies of each digit of a CTA's shared accumulator and add
+// the non-zero digits to the global accumulator.  Needs a __syncthreads()
+// before (all deposits done) -- the caller provides it.
+__device__ __forceinline__ void smem_to_global(const unsigned long long* sacc, unsigned long long* gacc) {
+  for (int k = threadIdx.x; k < kNDig; k += blockDim.x) {
+    unsigned long long s = 0;
+#pragma unroll
+    for (int c = 0; c < kCopies; c++) s += sacc[k * kCopies + c];
+    if (s) atomicAdd(gacc + k, s);
+  }
+}
+
+// Zero `nacc` shared-memory accumulators (kNDig * kCopies words each).
+__device__ __forceinline__ void smem_acc_zero(unsigned long long* sacc, int nacc = 1) {
+  for (int k = threadIdx.x; k < nacc * kNDig * kCopies; k += blockDim.x) sacc[k] = 0ull;
+}
+
+// ------------------------------------------------------------------ rounding
+
+// Normalise the carries of kNDig signed digits and round the value
+// sum_k dig[k] 2^(32k + kE0) once to the nearest binary64, ties to even,
+// with gradual underflow and overflow to +-inf.  An exact zero gives +0.
+// Runs on one thread; D is kNDig words of scratch (shared memory).
+static __device__ __noinline__ double round_digits(const long long* dig, uint32_t* D) {
+  long long c = 0;
+  for (int k = 0; k < kNDig; k++) {
+    const long long v = dig[k] + c;  // |dig| < 2^62, |c| < 2^31: no overflow
+    D[k] = (uint32_t)v;
+    c = v >> 32;  // arithmetic shift: floor division by 2^32
+  }
+  const bool negative = c < 0;  // the top digits are all-ones for a negative value
+  if (negative) {
+    unsigned long long carry = 1;
+    for (int k = 0; k < kNDig; k++) {
+      const unsigned long long t = (unsigned long long)(~D[k]) + carry;
+      D[k] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+  int kt = -1;
+  for (int k = kNDig - 1; k >= 0; k--) {
+    if (D[k]) { kt = k; break; }
+  }
+  if (kt < 0) return 0.0;
+  const int t = 32 * kt + 31 - __clz(D[kt]);  // index of the leading bit
+  int lsb = t - 52;
+  if (lsb < kSubLsb) lsb = kSubLsb;
+  // 64 bits starting at lsb
+  const int wi = lsb >> 5, bi = lsb & 31;
+  const unsigned long long lo = (unsigned long long)D[wi] | ((unsigned long long)(wi + 1 < kNDig ? D[wi + 1] : 0u) << 32);
+  const unsigned long long hi = (wi + 2 < kNDig) ? D[wi + 2] : 0u;
+  unsigned long long mant = bi ? ((lo >> bi) | (hi << (64 - bi))) : lo;
+  const int nbits = t - lsb + 1;  // 1 .. 53
+  mant &= (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
+  // round bit and sticky bits below it
+  const int rb_i = lsb - 1;
+  const uint32_t rbit = (D[rb_i >> 5] >> (rb_i & 31)) & 1u;
+  bool sticky = (D[rb_i >> 5] & ((1u << (rb_i & 31)) - 1u)) != 0u;
+  for (int k = (rb_i >> 5) - 1; k >= 0 && !sticky; k--) sticky = D[k] != 0u;
+  if (rbit && (sticky || (mant & 1ull))) mant += 1ull;
+  if (mant == (1ull << 53)) {
+    mant >>= 1;
+    lsb += 1;
+  }
+  unsigned long long bits;
+  if (mant >= (1ull << 52)) {
+    const int biased = lsb + kE0 + 1075;  // exponent field of mant * 2^(lsb + kE0)
+    if (biased >= 2047) bits = 0x7FF0000000000000ull;
+    else bits = ((unsigned long long)biased << 52) | (mant - (1ull << 52));
+  } else {
+    bits = mant;  // subnormal (lsb == kSubLsb)
+  }
+  if (negative) bits |= 0x8000000000000000ull;
+  return __longlong_as_double((long long)bits);
+}
+
+// ------------------------------------------------------------------ EFTs and FPEs
+
+// Alg. 1
+__device__ __forceinline__ void two_sum(double a, double b, double& r, double& s) {
+  r = __dadd_rn(a, b);
+  const double z = __dsub_rn(r, a);
+  s = __dadd_rn(__dsub_rn(a, __dsub_rn(r, z)), __dsub_rn(b, z));
+}
+
+// Alg. 2
+__device__ __forceinline__ void two_prod(double a, double b, double& r, double& s) {
+  r = __dmul_rn(a, b);
+  s = __fma_rn(a, b, -r);
+}
+
+// Alg. 4 with the early exit of Sec. 4.2; returns the value carried out of
+// the last of the p terms (0 when nothing was lost).
+__device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, double x) {
+#pragma unroll
+  for (int i = 0; i < kFpeMax; i++) {
+    if (i < p) {
+      double r, s;
+      two_sum(f[i], x, r, s);
+      f[i] = r;
+      x = s;
+      if (x == 0.0) break;
+    }
+  }
+  return x;
+}
+
+// Alg. 3: a += b; returns true if a term was lost.
+__device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[kFpeMax], int p) {
+  bool lost = false;
+#pragma unroll
+  for (int i = 0; i < kFpeMax; i++) {
+    if (i < p && b[i] != 0.0) lost |= fpe_accumulate(a, p, b[i]) != 0.0;
+  }
+  return lost;
+}
+
+constexpr double kTwoProdSafe = 0x1p-969;  // |a*b| >= this: twoprod's error term is exact
+
+// One element of the FPE dot: product into the result expansion, its error
+// into the error expansion.  Returns true if bits may have been lost.
+__device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&err)[kFpeMax], int p, double a, double b) {
+  double r, s;
+  two_prod(a, b, r, s);
+  bool lost = (a != 0.0) & (b != 0.0) & (fabs(r) < kTwoProdSafe);
+  lost |= !isfinite(r);
+  lost |= fpe_accumulate(res, p, r) != 0.0;
+  if (s != 0.0) lost |= fpe_accumulate(err, p, s) != 0.0;
+  return lost;
+}
+
+// ------------------------------------------------------------------ misc
+
+__device__ __forceinline__ bool is_last_block(unsigned int* counter) {
+  __shared__ bool last;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(counter, 1u);
+    last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Exact sum of up to kFpeMax doubles (used to round a merged expansion):
+// deposit each term into plain digits and round.  One thread.
+static __device__ __noinline__ double exact_sum_terms(const double* terms, int p, long long* dig, uint32_t* D) {
+  for (int k = 0; k < kNDig; k++) dig[k] = 0;
+  for (int i = 0; i < p; i++) {
+    const ExactProd e = exact_product(terms[i], 1.0);
+    if (!e.nz) continue;
+    const uint32_t w[5] = {e.w0, e.w1, e.w2, e.w3, e.w4};
+    for (int k = 0; k < 5; k++) {
+      const long long v = (long long)w[k];
+      dig[e.q + k] += e.neg ? -v : v;
+    }
+  }
+  return round_digits(dig, D);
+}
+
+}  // namespace rpcg

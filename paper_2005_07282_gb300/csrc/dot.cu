@@ -1,0 +1,298 @@
+// Standalone dot products: exact (long accumulator), FPE with exactness
+// flag, and the plain FP64 baseline; plus the library-wide host helpers.
+#include <cmath>
+#include <cstring>
+
+#include "device.cuh"
+#include "host.h"
+
+namespace rpcg {
+
+// ------------------------------------------------------------------ host helpers
+static thread_local char g_err[512];
+
+void set_error(const char* fmt, ...) {
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(g_err, sizeof(g_err), fmt, ap);
+  va_end(ap);
+}
+void clear_error() { g_err[0] = 0; }
+
+int sm_count() {
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 152;
+  if (!cache[dev]) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 152;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+// ------------------------------------------------------------------ scratch
+constexpr int kDotBlock = 256;
+constexpr int kDotMaxGrid = 2048;
+constexpr int kFpeDotMaxGrid = kDotBlock;  // the last CTA merges one expansion per thread
+
+struct DotScratch {
+  // zeroed before every launch (header)
+  unsigned long long digits[kNDig];
+  unsigned int counter;
+  unsigned int flags;  // bit 0: non-finite input; bit 1: an expansion lost bits
+  // written before being read (no clearing needed)
+  double partials[kDotMaxGrid];
+  double fpe[kFpeDotMaxGrid * kFpeMax];
+};
+constexpr size_t kDotScratchHeader = offsetof(DotScratch, partials);
+
+// ------------------------------------------------------------------ exact dot
+__device__ __forceinline__ void exact_step(Window& win, unsigned long long* sacc, int copy, bool& bad, double x,
+                                           double y) {
+  const ExactProd p = exact_product(x, y);
+  bad |= p.bad;
+  exact_deposit(win, sacc, copy, p);
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, DotScratch* ws, double* out) {
+  __shared__ unsigned long long sacc[kNDig * kCopies];
+  __shared__ long long sdig[kNDig];
+  __shared__ uint32_t sD[kNDig];
+  smem_acc_zero(sacc);
+  __syncthreads();
+  Window win;
+  window_init(win);
+  const int copy = threadIdx.x & (kCopies - 1);
+  bool bad = false;
+  const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * BLOCK;
+  if ((((uintptr_t)a | (uintptr_t)b) & 15) == 0) {
+    const double2* a2 = reinterpret_cast<const double2*>(a);
+    const double2* b2 = reinterpret_cast<const double2*>(b);
+    const int64_t n2 = n >> 1;
+    int64_t i = tid;
+    for (; i + 3 * nthr < n2; i += 4 * nthr) {
+      double2 x[4], y[4];
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        x[u] = __ldcs(a2 + i + u * nthr);
+        y[u] = __ldcs(b2 + i + u * nthr);
+      }
+#pragma unroll
+      for (int u = 0; u < 4; u++) {
+        exact_step(win, sacc, copy, bad, x[u].x, y[u].x);
+        exact_step(win, sacc, copy, bad, x[u].y, y[u].y);
+      }
+    }
+    for (; i < n2; i += nthr) {
+      const double2 x = __ldcs(a2 + i), y = __ldcs(b2 + i);
+      exact_step(win, sacc, copy, bad, x.x, y.x);
+      exact_step(win, sacc, copy, bad, x.y, y.y);
+    }
+    if ((n & 1) && tid == 0) exact_step(win, sacc, copy, bad, a[n - 1], b[n - 1]);
+  } else {
+    for (int64_t i = tid; i < n; i += nthr) exact_step(win, sacc, copy, bad, a[i], b[i]);
+  }
+  window_flush(win, sacc, copy);
+  if (bad) atomicOr(&ws->flags, 1u);
+  __syncthreads();
+  smem_to_global(sacc, ws->digits);
+  if (is_last_block(&ws->counter)) {
+    for (int k = threadIdx.x; k < kNDig; k += BLOCK) sdig[k] = (long long)atomicExch(&ws->digits[k], 0ull);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      const unsigned int f = atomicExch(&ws->flags, 0u);
+      *out = (f & 1u) ? __longlong_as_double(0x7FF8000000000000ll) : round_digits(sdig, sD);
+      ws->counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ FPE dot
+// Fixed-order tree merge of BLOCK expansions held in shared memory
+// (sf[t * kFpeMax + i]); the result ends in slot 0.  Returns (via *lost)
+// whether any fpesum dropped a term.
+template <int BLOCK>
+__device__ void fpe_tree(double* sf, int count, int p, int* lost) {
+  for (int stride = 1; stride < count; stride <<= 1) {
+    __syncthreads();
+    const int t = threadIdx.x;
+    if ((t % (2 * stride)) == 0 && t + stride < count) {
+      double A[kFpeMax], B[kFpeMax];
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) {
+        A[i] = sf[t * kFpeMax + i];
+        B[i] = sf[(t + stride) * kFpeMax + i];
+      }
+      if (fpe_sum(A, B, p)) atomicOr(lost, 1);
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = A[i];
+    }
+  }
+  __syncthreads();
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,
+                                                   const double* __restrict__ b, int p, DotScratch* ws, double* out,
+                                                   int32_t* exact) {
+  __shared__ double sf[BLOCK * kFpeMax];
+  __shared__ int slost;
+  __shared__ long long sdig[kNDig];
+  __shared__ uint32_t sD[kNDig];
+  if (threadIdx.x == 0) slost = 0;
+  double res[kFpeMax], err[kFpeMax];
+#pragma unroll
+  for (int i = 0; i < kFpeMax; i++) res[i] = err[i] = 0.0;
+  bool lost = false;
+  const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * BLOCK;
+  for (int64_t i = tid; i < n; i += nthr) lost |= fpe_dot_step(res, err, p, __ldcs(a + i), __ldcs(b + i));
+  lost |= fpe_sum(res, err, p);
+#pragma unroll
+  for (int i = 0; i < kFpeMax; i++) sf[threadIdx.x * kFpeMax + i] = res[i];
+  __syncthreads();
+  if (lost) atomicOr(&slost, 1);
+  fpe_tree<BLOCK>(sf, BLOCK, p, &slost);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < kFpeMax; i++) ws->fpe[blockIdx.x * kFpeMax + i] = sf[i];
+    if (slost) atomicOr(&ws->flags, 2u);
+  }
+  if (is_last_block(&ws->counter)) {
+    const int g = gridDim.x;
+    for (int t = threadIdx.x; t < BLOCK; t += BLOCK) {
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = (t < g) ? __ldcg(&ws->fpe[t * kFpeMax + i]) : 0.0;
+    }
+    if (threadIdx.x == 0) slost = 0;
+    fpe_tree<BLOCK>(sf, g, p, &slost);
+    if (threadIdx.x == 0) {
+      const unsigned int f = atomicExch(&ws->flags, 0u);
+      bool fin = true;
+      for (int i = 0; i < p; i++) fin &= isfinite(sf[i]);
+      const bool ok = fin && !(f & 2u) && !slost;
+      *out = fin ? exact_sum_terms(sf, p, sdig, sD) : __longlong_as_double(0x7FF8000000000000ll);
+      *exact = ok ? 1 : 0;
+      ws->counter = 0;
+    }
+  }
+}
+
+// ------------------------------------------------------------------ plain dot
+template <int BLOCK>
+__device__ __forceinline__ double block_sum_fixed(double v, double* sw) {
+  // fixed-shape tree: warp shuffles, then warp 0 over the warp sums
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sw[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < BLOCK / 32 ? sw[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+  }
+  return s;  // valid in thread 0
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_dot_plain(int64_t n, const double* __restrict__ a,
+                                                     const double* __restrict__ b, DotScratch* ws, double* out) {
+  __shared__ double sw[32];
+  double acc = 0.0;
+  const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
+  const int64_t nthr = (int64_t)gridDim.x * BLOCK;
+  for (int64_t i = tid; i < n; i += nthr) acc = __fma_rn(__ldcs(a + i), __ldcs(b + i), acc);
+  const double s = block_sum_fixed<BLOCK>(acc, sw);
+  if (threadIdx.x == 0) ws->partials[blockIdx.x] = s;
+  if (is_last_block(&ws->counter)) {
+    double v = 0.0;
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += BLOCK) v = __dadd_rn(v, __ldcg(&ws->partials[t]));
+    const double tot = block_sum_fixed<BLOCK>(v, sw);
+    if (threadIdx.x == 0) {
+      *out = tot;
+      ws->counter = 0;
+    }
+  }
+}
+
+static int dot_grid(int64_t n, int per_thread, int cap) {
+  int64_t want = (n + (int64_t)kDotBlock * per_thread - 1) / ((int64_t)kDotBlock * per_thread);
+  int64_t g = sm_count() * 4;
+  if (want < g) g = want;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (int)g;
+}
+
+}  // namespace rpcg
+
+using namespace rpcg;
+
+extern "C" {
+
+const char* rpcg_last_error(void) { return g_err; }
+
+const char* rpcg_status_string(int32_t s) {
+  switch (s) {
+    case RPCG_OK: return "ok";
+    case RPCG_NOT_CONVERGED: return "not converged";
+    case RPCG_FPE_INEXACT: return "floating-point expansion lost bits";
+    case RPCG_ERR_INVALID: return "invalid argument";
+    case RPCG_ERR_NOT_SPD: return "matrix not SPD (diagonal or curvature)";
+    case RPCG_ERR_NONFINITE: return "non-finite value";
+    case RPCG_ERR_OOM: return "out of device memory or budget";
+    case RPCG_ERR_CUDA: return "CUDA error";
+    case RPCG_ERR_TIMEOUT: return "timed out";
+    default: return "unknown status";
+  }
+}
+
+static rpcg_status dot_common(int kind, int64_t n, const double* a, const double* b, int32_t p, double* out,
+                              int32_t* exact, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(n >= 0 && n <= (int64_t(1) << 30), "n must be in [0, 2^30]");
+  RPCG_CHECK_ARG(out != nullptr, "out is NULL");
+  RPCG_CHECK_ARG(n == 0 || (a != nullptr && b != nullptr), "a or b is NULL");
+  RPCG_CHECK_ARG(kind != 1 || (p >= 1 && p <= kFpeMax && exact != nullptr), "fpe: p must be 1..8 and exact non-NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  DotScratch* ws = nullptr;
+  RPCG_CUDA_TRY(cudaMallocAsync((void**)&ws, sizeof(DotScratch), s));
+  cudaError_t e = cudaMemsetAsync(ws, 0, kDotScratchHeader, s);
+  if (e == cudaSuccess) {
+    if (kind == 0) {
+      k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
+    } else if (kind == 1) {
+      k_dot_fpe<kDotBlock><<<dot_grid(n, 4, kFpeDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
+    } else {
+      k_dot_plain<kDotBlock><<<dot_grid(n, 4, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
+    }
+    e = cudaGetLastError();
+  }
+  cudaFreeAsync(ws, s);
+  if (e != cudaSuccess) {
+    set_error("dot launch failed: %s", cudaGetErrorString(e));
+    return RPCG_ERR_CUDA;
+  }
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_dot_exact(int64_t n, const double* a, const double* b, double* out, void* stream) {
+  return dot_common(0, n, a, b, 0, out, nullptr, stream);
+}
+
+rpcg_status rpcg_dot_fpe(int64_t n, const double* a, const double* b, int32_t p, double* out, int32_t* exact,
+                         void* stream) {
+  return dot_common(1, n, a, b, p, out, exact, stream);
+}
+
+rpcg_status rpcg_dot_plain(int64_t n, const double* a, const double* b, double* out, void* stream) {
+  return dot_common(2, n, a, b, 0, out, nullptr, stream);
+}
+
+}  // extern "C"

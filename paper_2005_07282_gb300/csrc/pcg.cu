@@ -1,0 +1,1215 @@
+// Jacobi-PCG on one GPU: matrix handle, SpMV, the fused passes of one
+// iteration and the CUDA graph that runs the whole loop on the device.
+//
+// One iteration of Fig. 2 (S8 next to S6) is three streaming passes over
+// the vectors, each ending in a grid-wide reduction finished by the last
+// CTA to arrive (the single-GPU form of the paper's Reduce + Round + Bcast,
+// Listing 3 / Listing 4):
+//   pass A  S1 + S2   w = A d (rows summed left to right with fma) and the
+//                     dot <d, w> deposited from registers; last CTA: rho.
+//   pass B  S3-S6,S8  x = fma(rho, d, x), r = fma(-rho, w, r), z = inv .* r
+//                     (z is not stored), <z, r> and <r, r> deposited; last
+//                     CTA: beta, tau, gamma = beta / beta', relres, the loop
+//                     condition (cudaGraphSetConditional).
+//   pass C  S7        d = fma(gamma, d, inv .* r).
+// This merges S1 with S2 and S4 with S5 and S6 -- the task overlap of
+// Sec. 3.3 turned into kernel fusion.  The loop body is the child graph of a
+// conditional while node, so no host round trip happens per iteration.
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <tuple>
+#include <vector>
+
+#include "device.cuh"
+#include "host.h"
+
+namespace rpcg {
+
+constexpr int kMaxPassGrid = 4096;
+constexpr int kSpmvCapPerRow = 32;  // staged nnz per row of a tile (on average)
+
+// Per-solve arguments, written by the host before every launch of the graph.
+struct SolveArgs {
+  const double* b;
+  double* x;
+  double* history;
+  double tol;
+  int max_iter;
+  int fpe_size;
+  int fpe_strict;
+  int variant;
+  int use_cond;  // 1: running inside the graph (set the while node's condition)
+};
+
+// Solver state, device resident.
+struct SolveState {
+  double rho, beta, beta_old, tau, gamma, bnorm, rel;
+  int iter, status, bad_row, bzero, redo, fpe_inexact, active, pad;
+};
+
+// Grid-reduction scratch of one pass: up to three simultaneous dots.
+struct PassScratch {
+  unsigned long long digits[3][kNDig];  // exact: global accumulators (cleared by the last CTA)
+  unsigned int counter;                 // CTAs arrived (reset by the last CTA)
+  unsigned int flags;                   // bit 0: non-finite operand; bit 1 + j: dot j lost bits (fpe)
+  double partials[3][kMaxPassGrid];     // plain: CTA partial sums
+  double fpe[3][512][kFpeMax];          // fpe: CTA expansions (grid <= 512 for fpe)
+};
+
+struct CsrDev {
+  int n, nnz;
+  const int* rowptr;
+  const int* col;
+  const double* val;
+};
+
+// ------------------------------------------------------------------ reducers
+
+constexpr int kFpeTree = 512;  // expansions merged by one CTA (threads of a CTA, or CTAs of a grid)
+
+struct FinalScratch {  // shared memory of the CTA and grid reductions
+  double* fpe;         // kFpeTree expansions (fpe variant only)
+  long long dig[kNDig];
+  uint32_t D[kNDig];
+  double sw[32];
+  double value[3];
+  int lost[3];
+  int slost;
+  bool last;
+};
+
+
+// Per-thread state of NACC simultaneous dot products for variant V.
+template <int V, int NACC>
+struct Reducer {
+  Window win[NACC];          // exact
+  double res[NACC][kFpeMax]; // fpe
+  double err[NACC][kFpeMax];
+  double acc[NACC];          // plain
+  bool lost[NACC];
+  bool bad;
+};
+
+template <int V, int NACC>
+__device__ __forceinline__ void red_init(Reducer<V, NACC>& R) {
+#pragma unroll
+  for (int j = 0; j < NACC; j++) {
+    if constexpr (V == RPCG_EXBLAS) window_init(R.win[j]);
+    if constexpr (V == RPCG_FPE) {
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) R.res[j][i] = R.err[j][i] = 0.0;
+    }
+    if constexpr (V == RPCG_PLAIN) R.acc[j] = 0.0;
+    R.lost[j] = false;
+  }
+  R.bad = false;
+}
+
+// shared memory of the reducers: exact needs NACC accumulators with copies
+template <int V, int NACC>
+__host__ __device__ constexpr size_t red_smem_bytes() {
+  return V == RPCG_EXBLAS ? (size_t)NACC * kNDig * kCopies * sizeof(unsigned long long)
+                          : (V == RPCG_FPE ? (size_t)kFpeTree * kFpeMax * sizeof(double) : 0);
+}
+
+// Carve the reducer's shared memory: [exact accumulators | fpe tree] then FinalScratch.
+template <int V, int NACC>
+__device__ __forceinline__ FinalScratch* red_carve(unsigned char* base, unsigned long long*& sacc) {
+  sacc = reinterpret_cast<unsigned long long*>(base);
+  FinalScratch* fs = reinterpret_cast<FinalScratch*>(base + red_smem_bytes<V, NACC>());
+  if (threadIdx.x == 0) fs->fpe = reinterpret_cast<double*>(base);
+  return fs;
+}
+
+template <int V, int NACC>
+__device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long* sacc, int j, double a, double b,
+                                        int p) {
+  if constexpr (V == RPCG_EXBLAS) {
+    const ExactProd e = exact_product(a, b);
+    R.bad |= e.bad;
+    exact_deposit(R.win[j], sacc + j * kNDig * kCopies, threadIdx.x & (kCopies - 1), e);
+  } else if constexpr (V == RPCG_FPE) {
+    R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b);
+  } else {
+    R.acc[j] = __fma_rn(a, b, R.acc[j]);
+  }
+}
+
+template <int BLOCK>
+__device__ __forceinline__ double block_sum_fixed(double v, double* sw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sw[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < BLOCK / 32 ? sw[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+  }
+  return s;
+}
+
+template <int BLOCK>
+__device__ void fpe_tree_pass(double* sf, int count, int p, int* lost) {
+  for (int stride = 1; stride < count; stride <<= 1) {
+    __syncthreads();
+    for (int t = threadIdx.x * 2 * stride; t + stride < count; t += BLOCK * 2 * stride) {
+      double A[kFpeMax], B[kFpeMax];
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) {
+        A[i] = sf[t * kFpeMax + i];
+        B[i] = sf[(t + stride) * kFpeMax + i];
+      }
+      if (fpe_sum(A, B, p)) atomicOr(lost, 1);
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = A[i];
+    }
+  }
+  __syncthreads();
+}
+
+// CTA part of the reduction (all threads), then the grid part by the last
+// CTA.  Returns true in every thread of the last CTA; fs->value[j] then
+// holds the dot values and fs->lost[j] whether an expansion lost bits (fpe)
+// or an operand was non-finite (all variants report NaN for those).
+template <int V, int NACC, int BLOCK>
+__device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassScratch* ws, FinalScratch* fs, int p) {
+  const int copy = threadIdx.x & (kCopies - 1);
+  if constexpr (V == RPCG_EXBLAS) {
+#pragma unroll
+    for (int j = 0; j < NACC; j++) window_flush(R.win[j], sacc + j * kNDig * kCopies, copy);
+    if (R.bad) atomicOr(&ws->flags, 1u);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, ws->digits[j]);
+  } else if constexpr (V == RPCG_FPE) {
+    for (int j = 0; j < NACC; j++) {
+      R.lost[j] |= fpe_sum(R.res[j], R.err[j], p);
+      __syncthreads();
+      if (threadIdx.x == 0) fs->slost = 0;
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) fs->fpe[threadIdx.x * kFpeMax + i] = R.res[j][i];
+      __syncthreads();
+      if (R.lost[j]) atomicOr(&fs->slost, 1);
+      fpe_tree_pass<BLOCK>(fs->fpe, BLOCK, p, &fs->slost);
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < kFpeMax; i++) ws->fpe[j][blockIdx.x][i] = fs->fpe[i];
+        if (fs->slost) atomicOr(&ws->flags, 2u << j);
+      }
+    }
+  } else {
+    for (int j = 0; j < NACC; j++) {
+      const double s = block_sum_fixed<BLOCK>(R.acc[j], fs->sw);
+      if (threadIdx.x == 0) ws->partials[j][blockIdx.x] = s;
+    }
+  }
+  // arrival
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const unsigned int prev = atomicAdd(&ws->counter, 1u);
+    fs->last = (prev == gridDim.x - 1);
+  }
+  __syncthreads();
+  if (!fs->last) return false;
+  __threadfence();
+  if constexpr (V == RPCG_EXBLAS) {
+    for (int j = 0; j < NACC; j++) {
+      for (int k = threadIdx.x; k < kNDig; k += BLOCK) fs->dig[k] = (long long)atomicExch(&ws->digits[j][k], 0ull);
+      __syncthreads();
+      if (threadIdx.x == 0) fs->value[j] = round_digits(fs->dig, fs->D);
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const unsigned int f = atomicExch(&ws->flags, 0u);
+      for (int j = 0; j < NACC; j++) {
+        fs->lost[j] = (f & 1u) ? 1 : 0;
+        if (f & 1u) fs->value[j] = __longlong_as_double(0x7FF8000000000000ll);
+      }
+    }
+  } else if constexpr (V == RPCG_FPE) {
+    const int g = gridDim.x;
+    for (int j = 0; j < NACC; j++) {
+      for (int t = threadIdx.x; t < g; t += BLOCK) {
+#pragma unroll
+        for (int i = 0; i < kFpeMax; i++) fs->fpe[t * kFpeMax + i] = __ldcg(&ws->fpe[j][t][i]);
+      }
+      if (threadIdx.x == 0) fs->slost = 0;
+      fpe_tree_pass<BLOCK>(fs->fpe, g, p, &fs->slost);
+      if (threadIdx.x == 0) {
+        bool fin = true;
+        for (int i = 0; i < p; i++) fin &= isfinite(fs->fpe[i]);
+        fs->value[j] = fin ? exact_sum_terms(fs->fpe, p, fs->dig, fs->D) : __longlong_as_double(0x7FF8000000000000ll);
+        fs->lost[j] = (fs->slost || !fin) ? 1 : 0;
+      }
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+      const unsigned int f = atomicExch(&ws->flags, 0u);
+      for (int j = 0; j < NACC; j++) fs->lost[j] |= (f & (2u << j)) ? 1 : 0;
+    }
+  } else {
+    for (int j = 0; j < NACC; j++) {
+      double v = 0.0;
+      for (int t = threadIdx.x; t < (int)gridDim.x; t += BLOCK) v = __dadd_rn(v, __ldcg(&ws->partials[j][t]));
+      const double s = block_sum_fixed<BLOCK>(v, fs->sw);
+      if (threadIdx.x == 0) {
+        fs->value[j] = s;
+        fs->lost[j] = 0;
+      }
+    }
+  }
+  if (threadIdx.x == 0) ws->counter = 0;
+  __syncthreads();
+  return true;
+}
+
+// ------------------------------------------------------------------ scalar steps (one thread)
+
+__device__ __forceinline__ void set_cond(const SolveArgs* args, cudaGraphConditionalHandle cond, bool go) {
+  if (args->use_cond) cudaGraphSetConditional(cond, go ? 1u : 0u);
+}
+
+__device__ void stop_loop(SolveState* st, const SolveArgs* args, cudaGraphConditionalHandle cond) {
+  st->active = 0;
+  set_cond(args, cond, false);
+}
+
+// S2: rho = beta / <d, w> (with the breakdown checks).
+__device__ void finalize_a(double dw, SolveState* st, const SolveArgs* args, cudaGraphConditionalHandle cond) {
+  if (!isfinite(dw)) {
+    st->status = RPCG_ERR_NONFINITE;
+    stop_loop(st, args, cond);
+    return;
+  }
+  if (!(dw > 0.0)) {
+    st->status = RPCG_ERR_NOT_SPD;
+    stop_loop(st, args, cond);
+    return;
+  }
+  st->beta_old = st->beta;
+  st->rho = __ddiv_rn(st->beta, dw);
+}
+
+// After S6 and S8: gamma for S7, the iteration count, relres and the loop test.
+__device__ void finalize_b(double beta, double tau, SolveState* st, const SolveArgs* args,
+                           cudaGraphConditionalHandle cond) {
+  st->beta = beta;
+  st->tau = tau;
+  if (!isfinite(beta) || !isfinite(tau)) {
+    st->status = RPCG_ERR_NONFINITE;
+    st->iter += 1;
+    stop_loop(st, args, cond);
+    return;
+  }
+  st->gamma = __ddiv_rn(beta, st->beta_old);
+  st->iter += 1;
+  st->rel = __ddiv_rn(__dsqrt_rn(tau), st->bnorm);
+  if (args->history) args->history[st->iter] = st->rel;
+  if (tau > 0.0 && !(beta > 0.0)) {
+    st->status = RPCG_ERR_NOT_SPD;
+    stop_loop(st, args, cond);
+    return;
+  }
+  const bool go = (st->rel >= args->tol) && (st->iter < args->max_iter);
+  st->active = go;
+  set_cond(args, cond, go);
+}
+
+// ------------------------------------------------------------------ kernels
+
+__global__ void k_init_state(SolveState* st, int n) {
+  st->rho = st->beta = st->beta_old = st->gamma = st->bnorm = 0.0;
+  st->tau = st->rel = __longlong_as_double(0x7FF8000000000000ll);
+  st->iter = 0;
+  st->status = 0;
+  st->bad_row = INT_MAX;
+  st->bzero = 0;
+  st->redo = 0;
+  st->fpe_inexact = 0;
+  st->active = 0;
+}
+
+// Jacobi preconditioner (Sec. 3.1, Sec. 4.3): inv_i = RN(1 / a_ii).  Rows
+// without a positive finite diagonal are recorded (lowest index wins).
+__global__ void k_inv_diag(CsrDev m, double* inv, SolveState* st) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
+    double aii = 0.0;
+    bool found = false;
+    for (int k = m.rowptr[i]; k < m.rowptr[i + 1]; k++) {
+      if (m.col[k] == i) {
+        aii = m.val[k];
+        found = true;
+      }
+    }
+    if (!found || !(aii > 0.0)) {
+      atomicMin(&st->bad_row, i);
+      inv[i] = 0.0;
+    } else {
+      inv[i] = __drcp_rn(aii);
+    }
+  }
+}
+
+// One tile of BLOCK rows of y = A x, rows summed left to right with fma
+// from +0 (Sec. 4.3).  The tile's CSR slab is staged in shared memory with
+// coalesced loads when it fits; otherwise rows read global memory directly.
+template <int BLOCK>
+__device__ __forceinline__ double spmv_tile(const CsrDev& m, const double* __restrict__ x, int tile, double* s_val,
+                                            int* s_col, int cap, int& row) {
+  const int r0 = tile * BLOCK;
+  const int r1 = min(r0 + BLOCK, m.n);
+  const int k0 = __ldg(m.rowptr + r0);
+  const int k1 = __ldg(m.rowptr + r1);
+  const int cnt = k1 - k0;
+  const bool staged = cnt <= cap;
+  __syncthreads();  // the previous tile is done with the slab
+  if (staged) {
+    for (int k = threadIdx.x; k < cnt; k += BLOCK) {
+      s_val[k] = __ldcs(m.val + k0 + k);
+      s_col[k] = __ldcs(m.col + k0 + k);
+    }
+  }
+  __syncthreads();
+  row = r0 + threadIdx.x;
+  double acc = 0.0;
+  if (row < m.n) {
+    const int a = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
+    if (staged) {
+      for (int k = a - k0; k < e - k0; k++) acc = __fma_rn(s_val[k], __ldg(x + s_col[k]), acc);
+    } else {
+      for (int k = a; k < e; k++) acc = __fma_rn(__ldg(m.val + k), __ldg(x + __ldg(m.col + k)), acc);
+    }
+  }
+  return acc;
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_spmv(CsrDev m, const double* __restrict__ x, double* __restrict__ y) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int cap = BLOCK * kSpmvCapPerRow;
+  double* s_val = reinterpret_cast<double*>(smem);
+  int* s_col = reinterpret_cast<int*>(s_val + cap);
+  const int ntiles = (m.n + BLOCK - 1) / BLOCK;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int row;
+    const double v = spmv_tile<BLOCK>(m, x, tile, s_val, s_col, cap, row);
+    if (row < m.n) y[row] = v;
+  }
+}
+
+// Pass A: S1 + S2.
+template <int V, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_pass_a(CsrDev m, const double* __restrict__ d, double* __restrict__ w,
+                                                  PassScratch* ws, SolveState* st, const SolveArgs* args,
+                                                  cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int cap = BLOCK * kSpmvCapPerRow;
+  double* s_val = reinterpret_cast<double*>(smem);
+  int* s_col = reinterpret_cast<int*>(s_val + cap);
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<V, 1>(reinterpret_cast<unsigned char*>(s_col + cap), sacc);
+  if (st->status != 0) return;
+  const int p = args->fpe_size;
+  if constexpr (V == RPCG_EXBLAS) {
+    smem_acc_zero(sacc);
+  }
+  Reducer<V, 1> R;
+  red_init(R);
+  const int ntiles = (m.n + BLOCK - 1) / BLOCK;
+  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    int row;
+    const double v = spmv_tile<BLOCK>(m, d, tile, s_val, s_col, cap, row);
+    if (row < m.n) {
+      w[row] = v;
+      red_add(R, sacc, 0, __ldg(d + row), v, p);
+    }
+  }
+  if (red_finish<V, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
+    if (V == RPCG_FPE && fs->lost[0]) {
+      st->fpe_inexact += 1;
+      if (!args->fpe_strict) {
+        st->redo = 1;  // recompute this dot exactly (k_redo_a)
+        return;
+      }
+    }
+    finalize_a(fs->value[0], st, args, cond);
+  }
+}
+
+// Pass B: S3, S4, S5, S6 and S8.
+template <int V, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restrict__ d, const double* __restrict__ w,
+                                                  const double* __restrict__ inv, double* __restrict__ r,
+                                                  PassScratch* ws, SolveState* st, const SolveArgs* args,
+                                                  cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<V, 2>(smem, sacc);
+  if (st->status != 0 || st->redo) return;
+  const int p = args->fpe_size;
+  double* __restrict__ x = args->x;
+  const double rho = st->rho, nrho = -st->rho;
+  if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc, 2);
+  __syncthreads();
+  Reducer<V, 2> R;
+  red_init(R);
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const double di = __ldcs(d + i), wi = __ldcs(w + i), ivi = __ldcs(inv + i);
+    const double xi = __fma_rn(rho, di, __ldcs(x + i));
+    const double ri = __fma_rn(nrho, wi, __ldcs(r + i));
+    const double zi = __dmul_rn(ivi, ri);
+    __stcs(x + i, xi);
+    __stcs(r + i, ri);
+    red_add(R, sacc, 0, zi, ri, p);
+    red_add(R, sacc, 1, ri, ri, p);
+  }
+  if (red_finish<V, 2, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
+    if (V == RPCG_FPE && (fs->lost[0] || fs->lost[1])) {
+      st->fpe_inexact += (fs->lost[0] ? 1 : 0) + (fs->lost[1] ? 1 : 0);
+      if (!args->fpe_strict) {
+        st->redo = 2;  // recompute both dots exactly (k_redo_b)
+        return;
+      }
+    }
+    finalize_b(fs->value[0], fs->value[1], st, args, cond);
+  }
+}
+
+// Pass C: S7.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_pass_c(int n, double* __restrict__ d, const double* __restrict__ inv,
+                                                  const double* __restrict__ r, const SolveState* st) {
+  if (st->status != 0) return;
+  const double g = st->gamma;
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const double zi = __dmul_rn(__ldcs(inv + i), __ldcs(r + i));
+    d[i] = __fma_rn(g, d[i], zi);
+  }
+}
+
+// FPE variant with fpe_strict = 0: an inexact dot is recomputed exactly.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_redo_a(int n, const double* __restrict__ d, const double* __restrict__ w,
+                                                  PassScratch* ws, SolveState* st, const SolveArgs* args,
+                                                  cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<RPCG_EXBLAS, 1>(smem, sacc);
+  if (st->redo != 1) return;
+  smem_acc_zero(sacc);
+  Reducer<RPCG_EXBLAS, 1> R;
+  red_init(R);
+  __syncthreads();
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) red_add(R, sacc, 0, d[i], w[i], 0);
+  if (red_finish<RPCG_EXBLAS, 1, BLOCK>(R, sacc, ws, fs, 0) && threadIdx.x == 0) {
+    st->redo = 0;
+    finalize_a(fs->value[0], st, args, cond);
+  }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_redo_b(int n, const double* __restrict__ inv, const double* __restrict__ r,
+                                                  PassScratch* ws, SolveState* st, const SolveArgs* args,
+                                                  cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<RPCG_EXBLAS, 2>(smem, sacc);
+  if (st->redo != 2) return;
+  smem_acc_zero(sacc, 2);
+  Reducer<RPCG_EXBLAS, 2> R;
+  red_init(R);
+  __syncthreads();
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const double ri = r[i];
+    const double zi = __dmul_rn(inv[i], ri);
+    red_add(R, sacc, 0, zi, ri, 0);
+    red_add(R, sacc, 1, ri, ri, 0);
+  }
+  if (red_finish<RPCG_EXBLAS, 2, BLOCK>(R, sacc, ws, fs, 0) && threadIdx.x == 0) {
+    st->redo = 0;
+    finalize_b(fs->value[0], fs->value[1], st, args, cond);
+  }
+}
+
+// Set-up: r0 = b - A x0 (A x0 already in w), z0 = inv .* r0, d0 = z0,
+// beta0 = <z0, r0>, tau0 = <r0, r0>, ||b||^2 = <b, b>; last CTA: checks,
+// relres0 and the initial loop condition.  The set-up dots are always exact
+// (plain for the plain variant).
+template <int V, int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_setup(CsrDev m, const double* __restrict__ q, const double* __restrict__ inv,
+                                                 double* __restrict__ r, double* __restrict__ d, PassScratch* ws,
+                                                 SolveState* st, const SolveArgs* args,
+                                                 cudaGraphConditionalHandle cond) {
+  // the set-up dots are exact for both reproducible variants
+  constexpr int VS = (V == RPCG_PLAIN) ? RPCG_PLAIN : RPCG_EXBLAS;
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<VS, 3>(smem, sacc);
+  const int n = m.n;
+  const double* __restrict__ b = args->b;
+  if constexpr (VS == RPCG_EXBLAS) smem_acc_zero(sacc, 3);
+  Reducer<VS, 3> R;
+  red_init(R);
+  __syncthreads();
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const double bi = b[i];
+    const double ri = __dsub_rn(bi, q[i]);
+    const double zi = __dmul_rn(inv[i], ri);
+    r[i] = ri;
+    d[i] = zi;
+    red_add(R, sacc, 0, zi, ri, 0);
+    red_add(R, sacc, 1, ri, ri, 0);
+    red_add(R, sacc, 2, bi, bi, 0);
+  }
+  if (red_finish<VS, 3, BLOCK>(R, sacc, ws, fs, 0) && threadIdx.x == 0) {
+    if (st->bad_row < n) {
+      // the lowest-index row without a positive finite diagonal decides
+      const int i = st->bad_row;
+      double aii = 0.0;
+      for (int k = m.rowptr[i]; k < m.rowptr[i + 1]; k++)
+        if (m.col[k] == i) aii = m.val[k];
+      st->status = isfinite(aii) ? RPCG_ERR_NOT_SPD : RPCG_ERR_NONFINITE;
+      stop_loop(st, args, cond);
+      return;
+    }
+    const double beta = fs->value[0], tau = fs->value[1], bb = fs->value[2];
+    if (!isfinite(beta) || !isfinite(tau) || !isfinite(bb)) {
+      st->status = RPCG_ERR_NONFINITE;
+      stop_loop(st, args, cond);
+      return;
+    }
+    st->beta = beta;
+    const double bnorm = __dsqrt_rn(bb);
+    st->bnorm = bnorm;
+    if (bnorm == 0.0) {
+      st->bzero = 1;
+      st->rel = 0.0;
+      st->tau = 0.0;
+      if (args->history) args->history[0] = 0.0;
+      stop_loop(st, args, cond);
+      return;
+    }
+    st->tau = tau;
+    st->rel = __ddiv_rn(__dsqrt_rn(tau), bnorm);
+    if (args->history) args->history[0] = st->rel;
+    const bool go = (st->rel >= args->tol) && (0 < args->max_iter);
+    st->active = go;
+    set_cond(args, cond, go);
+  }
+}
+
+// ------------------------------------------------------------------ handle
+
+struct GraphKey {
+  int variant, block, grid;
+  bool operator<(const GraphKey& o) const {
+    return std::tie(variant, block, grid) < std::tie(o.variant, o.block, o.grid);
+  }
+};
+
+}  // namespace rpcg
+
+struct rpcg_matrix_s {
+  rpcg::CsrDev m{};
+  int* rowptr = nullptr;
+  int* col = nullptr;
+  double* val = nullptr;
+  double* inv = nullptr;
+  double* r = nullptr;
+  double* d = nullptr;
+  double* w = nullptr;
+  double* bx = nullptr;  // staging for rpcg_solve_host: b then x
+  rpcg::SolveArgs* args = nullptr;
+  rpcg::SolveState* state = nullptr;
+  rpcg::PassScratch* scratch = nullptr;
+  rpcg::SolveArgs* h_args = nullptr;    // pinned
+  rpcg::SolveState* h_state = nullptr;  // pinned
+  std::map<rpcg::GraphKey, cudaGraphExec_t> graphs;
+  std::map<rpcg::GraphKey, cudaGraph_t> graph_defs;
+  std::map<rpcg::GraphKey, cudaGraphNode_t> x0_nodes;
+  int device = 0;
+};
+
+namespace rpcg {
+
+static int pick_block(int b) { return (b == 128 || b == 256 || b == 512) ? b : 256; }
+
+template <int BLOCK>
+static size_t spmv_smem() {
+  return (size_t)BLOCK * kSpmvCapPerRow * (sizeof(double) + sizeof(int));
+}
+
+template <int V, int NACC>
+static size_t pass_smem() {
+  return red_smem_bytes<V, NACC>() + sizeof(FinalScratch) + 16;
+}
+
+static cudaError_t add_kernel(cudaGraph_t g, cudaGraphNode_t* node, const cudaGraphNode_t* deps, int ndeps,
+                              const void* func, int grid, int block, size_t smem, void** args) {
+  cudaKernelNodeParams p{};
+  p.func = const_cast<void*>(func);
+  p.gridDim = dim3(grid);
+  p.blockDim = dim3(block);
+  p.sharedMemBytes = (unsigned)smem;
+  p.kernelParams = args;
+  p.extra = nullptr;
+  return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
+}
+
+template <typename F>
+static cudaError_t set_smem(F* f, size_t bytes) {
+  return cudaFuncSetAttribute((const void*)f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// Grid sizes and shared memory of every kernel of a solve.
+struct LaunchCfg {
+  int grid_stream, grid_tiles, grid_small;
+  size_t smem_spmv, smem_a, smem_b, smem_s, smem_ra, smem_rb;
+};
+
+template <int V, int BLOCK>
+static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
+  const int sms = sm_count();
+  const int ntiles = (n + BLOCK - 1) / BLOCK;
+  int grid_stream = grid > 0 ? grid : sms * (BLOCK >= 512 ? 2 : 4);
+  int grid_tiles = grid > 0 ? grid : sms * 2;
+  if (V == RPCG_FPE) {
+    if (grid_stream > 512) grid_stream = 512;
+    if (grid_tiles > 512) grid_tiles = 512;
+  }
+  if (grid_stream > kMaxPassGrid) grid_stream = kMaxPassGrid;
+  if (grid_tiles > kMaxPassGrid) grid_tiles = kMaxPassGrid;
+  if (grid_tiles > ntiles) grid_tiles = ntiles > 0 ? ntiles : 1;
+  const int grid_elem_cap = (n + BLOCK - 1) / BLOCK;
+  if (grid_stream > grid_elem_cap) grid_stream = grid_elem_cap > 0 ? grid_elem_cap : 1;
+  const int grid_small = (n + BLOCK - 1) / BLOCK > 0 ? ((n + BLOCK - 1) / BLOCK < sms * 8 ? (n + BLOCK - 1) / BLOCK : sms * 8) : 1;
+  c->grid_stream = grid_stream;
+  c->grid_tiles = grid_tiles;
+  c->grid_small = grid_small;
+  c->smem_spmv = spmv_smem<BLOCK>();
+  c->smem_a = c->smem_spmv + pass_smem<V, 1>();
+  c->smem_b = pass_smem<V, 2>();
+  c->smem_s = pass_smem<(V == RPCG_PLAIN ? RPCG_PLAIN : RPCG_EXBLAS), 3>();
+  c->smem_ra = pass_smem<RPCG_EXBLAS, 1>();
+  c->smem_rb = pass_smem<RPCG_EXBLAS, 2>();
+  RPCG_CUDA_TRY(set_smem(k_spmv<BLOCK>, c->smem_spmv));
+  RPCG_CUDA_TRY(set_smem(k_pass_a<V, BLOCK>, c->smem_a));
+  RPCG_CUDA_TRY(set_smem(k_pass_b<V, BLOCK>, c->smem_b));
+  RPCG_CUDA_TRY(set_smem(k_setup<V, BLOCK>, c->smem_s));
+  RPCG_CUDA_TRY(set_smem(k_redo_a<BLOCK>, c->smem_ra));
+  RPCG_CUDA_TRY(set_smem(k_redo_b<BLOCK>, c->smem_rb));
+  return RPCG_OK;
+}
+
+// Build the solve graph for one (variant, block, grid).
+template <int V, int BLOCK>
+static rpcg_status build_graph(rpcg_matrix_t A, int grid, cudaGraph_t* out_graph, cudaGraphExec_t* out_exec,
+                               cudaGraphNode_t* out_x0_node) {
+  CsrDev m = A->m;
+  int n = m.n;
+  LaunchCfg c;
+  rpcg_status cs = launch_cfg<V, BLOCK>(n, grid, &c);
+  if (cs != RPCG_OK) return cs;
+  const int grid_stream = c.grid_stream, grid_tiles = c.grid_tiles, grid_small = c.grid_small;
+  const size_t smem_spmv = c.smem_spmv, smem_a = c.smem_a, smem_b = c.smem_b, smem_s = c.smem_s;
+  const size_t smem_ra = c.smem_ra, smem_rb = c.smem_rb;
+  cudaGraph_t g = nullptr;
+  RPCG_CUDA_TRY(cudaGraphCreate(&g, 0));
+  cudaGraphConditionalHandle cond;
+  RPCG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
+  SolveState* st = A->state;
+  SolveArgs* args = A->args;
+  PassScratch* ws = A->scratch;
+  double *inv = A->inv, *r = A->r, *d = A->d, *w = A->w;
+
+  cudaGraphNode_t n_init, n_inv, n_spmv, n_setup, n_loop;
+  {
+    void* a[] = {&st, &n};
+    RPCG_CUDA_TRY(add_kernel(g, &n_init, nullptr, 0, (const void*)k_init_state, 1, 1, 0, a));
+  }
+  {
+    void* a[] = {&m, &inv, &st};
+    RPCG_CUDA_TRY(add_kernel(g, &n_inv, &n_init, 1, (const void*)k_inv_diag, grid_small, BLOCK, 0, a));
+  }
+  // q = A x0 into w.  The kernel reads x0 through its parameter, which
+  // set_x0() points at the caller's x before every launch.
+  {
+    const double* x0 = nullptr;
+    void* a[] = {&m, &x0, &w};
+    RPCG_CUDA_TRY(add_kernel(g, &n_spmv, &n_inv, 1, (const void*)k_spmv<BLOCK>, grid_tiles, BLOCK, smem_spmv, a));
+  }
+  {
+    void* a[] = {&m, &w, &inv, &r, &d, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(g, &n_setup, &n_spmv, 1, (const void*)k_setup<V, BLOCK>, grid_stream, BLOCK, smem_s, a));
+  }
+  // the while loop
+  cudaGraphNodeParams cp{};
+  cp.type = cudaGraphNodeTypeConditional;
+  cp.conditional.handle = cond;
+  cp.conditional.type = cudaGraphCondTypeWhile;
+  cp.conditional.size = 1;
+  RPCG_CUDA_TRY(cudaGraphAddNode(&n_loop, g, &n_setup, nullptr, 1, &cp));
+  cudaGraph_t body = cp.conditional.phGraph_out[0];
+  cudaGraphNode_t b_a, b_ra, b_b, b_rb, b_c;
+  {
+    void* a[] = {&m, &d, &w, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_a, nullptr, 0, (const void*)k_pass_a<V, BLOCK>, grid_tiles, BLOCK, smem_a, a));
+  }
+  cudaGraphNode_t prev = b_a;
+  if (V == RPCG_FPE) {
+    void* a[] = {&n, &d, &w, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_ra, &prev, 1, (const void*)k_redo_a<BLOCK>, grid_stream, BLOCK, smem_ra, a));
+    prev = b_ra;
+  }
+  {
+    void* a[] = {&n, &d, &w, &inv, &r, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_b, &prev, 1, (const void*)k_pass_b<V, BLOCK>, grid_stream, BLOCK, smem_b, a));
+    prev = b_b;
+  }
+  if (V == RPCG_FPE) {
+    void* a[] = {&n, &inv, &r, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_rb, &prev, 1, (const void*)k_redo_b<BLOCK>, grid_stream, BLOCK, smem_rb, a));
+    prev = b_rb;
+  }
+  {
+    void* a[] = {&n, &d, &inv, &r, &st};
+    RPCG_CUDA_TRY(add_kernel(body, &b_c, &prev, 1, (const void*)k_pass_c<BLOCK>, grid_stream, BLOCK, 0, a));
+  }
+  cudaGraphExec_t exec = nullptr;
+  RPCG_CUDA_TRY(cudaGraphInstantiate(&exec, g, 0));
+  *out_graph = g;
+  *out_exec = exec;
+  *out_x0_node = n_spmv;
+  return RPCG_OK;
+}
+
+template <int BLOCK>
+static rpcg_status build_graph_v(rpcg_matrix_t A, int v, int grid, cudaGraph_t* g, cudaGraphExec_t* e,
+                                 cudaGraphNode_t* x0) {
+  if (v == RPCG_PLAIN) return build_graph<RPCG_PLAIN, BLOCK>(A, grid, g, e, x0);
+  if (v == RPCG_EXBLAS) return build_graph<RPCG_EXBLAS, BLOCK>(A, grid, g, e, x0);
+  return build_graph<RPCG_FPE, BLOCK>(A, grid, g, e, x0);
+}
+
+static rpcg_status get_graph(rpcg_matrix_t A, int v, int block, int grid, cudaGraphExec_t* exec) {
+  GraphKey key{v, block, grid};
+  auto it = A->graphs.find(key);
+  if (it != A->graphs.end()) {
+    *exec = it->second;
+    return RPCG_OK;
+  }
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t e = nullptr;
+  cudaGraphNode_t x0 = nullptr;
+  rpcg_status s;
+  if (block == 128) s = build_graph_v<128>(A, v, grid, &g, &e, &x0);
+  else if (block == 512) s = build_graph_v<512>(A, v, grid, &g, &e, &x0);
+  else s = build_graph_v<256>(A, v, grid, &g, &e, &x0);
+  if (s != RPCG_OK) {
+    if (g) cudaGraphDestroy(g);
+    return s;
+  }
+  A->graphs[key] = e;
+  A->graph_defs[key] = g;
+  A->x0_nodes[key] = x0;
+  *exec = e;
+  return RPCG_OK;
+}
+
+// The same kernels launched one by one, with CUDA events around each pass
+// (pass_ms: set-up, A, B, C totals in milliseconds; launches: counts).
+template <int V, int BLOCK>
+static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaStream_t s, float* pass_ms,
+                             int* launches) {
+  CsrDev m = A->m;
+  const int n = m.n;
+  LaunchCfg c;
+  rpcg_status cs = launch_cfg<V, BLOCK>(n, grid, &c);
+  if (cs != RPCG_OK) return cs;
+  SolveState* st = A->state;
+  SolveArgs* args = A->args;
+  PassScratch* ws = A->scratch;
+  double *inv = A->inv, *r = A->r, *d = A->d, *w = A->w;
+  const cudaGraphConditionalHandle cond = 0;
+  cudaEvent_t ev[8];
+  for (auto& e : ev) RPCG_CUDA_TRY(cudaEventCreate(&e));
+  float acc[4] = {0, 0, 0, 0};
+  int cnt[4] = {0, 0, 0, 0};
+  auto fail = [&](cudaError_t e) {
+    for (auto& x : ev) cudaEventDestroy(x);
+    set_error("eager solve: %s", cudaGetErrorString(e));
+    return RPCG_ERR_CUDA;
+  };
+  cudaError_t e;
+  e = cudaEventRecord(ev[0], s);
+  k_init_state<<<1, 1, 0, s>>>(st, n);
+  k_inv_diag<<<c.grid_small, BLOCK, 0, s>>>(m, inv, st);
+  k_spmv<BLOCK><<<c.grid_tiles, BLOCK, c.smem_spmv, s>>>(m, x0, w);
+  k_setup<V, BLOCK><<<c.grid_stream, BLOCK, c.smem_s, s>>>(m, w, inv, r, d, ws, st, args, cond);
+  cudaEventRecord(ev[1], s);
+  if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+  if ((e = cudaMemcpyAsync(A->h_state, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s)) != cudaSuccess) return fail(e);
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
+  float t;
+  cudaEventElapsedTime(&t, ev[0], ev[1]);
+  acc[0] += t;
+  cnt[0] += 1;
+  while (A->h_state->active) {
+    cudaEventRecord(ev[2], s);
+    k_pass_a<V, BLOCK><<<c.grid_tiles, BLOCK, c.smem_a, s>>>(m, d, w, ws, st, args, cond);
+    cudaEventRecord(ev[3], s);
+    if (V == RPCG_FPE) k_redo_a<BLOCK><<<c.grid_stream, BLOCK, c.smem_ra, s>>>(n, d, w, ws, st, args, cond);
+    cudaEventRecord(ev[4], s);
+    k_pass_b<V, BLOCK><<<c.grid_stream, BLOCK, c.smem_b, s>>>(n, d, w, inv, r, ws, st, args, cond);
+    cudaEventRecord(ev[5], s);
+    if (V == RPCG_FPE) k_redo_b<BLOCK><<<c.grid_stream, BLOCK, c.smem_rb, s>>>(n, inv, r, ws, st, args, cond);
+    cudaEventRecord(ev[6], s);
+    k_pass_c<BLOCK><<<c.grid_stream, BLOCK, 0, s>>>(n, d, inv, r, st);
+    cudaEventRecord(ev[7], s);
+    if ((e = cudaGetLastError()) != cudaSuccess) return fail(e);
+    if ((e = cudaMemcpyAsync(A->h_state, st, sizeof(SolveState), cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      return fail(e);
+    if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return fail(e);
+    cudaEventElapsedTime(&t, ev[2], ev[3]);
+    acc[1] += t;
+    cudaEventElapsedTime(&t, ev[4], ev[5]);
+    acc[2] += t;
+    cudaEventElapsedTime(&t, ev[6], ev[7]);
+    acc[3] += t;
+    cnt[1] += 1;
+    cnt[2] += 1;
+    cnt[3] += 1;
+    if (A->h_state->status != 0) break;
+  }
+  for (auto& x : ev) cudaEventDestroy(x);
+  for (int i = 0; i < 4; i++) {
+    if (pass_ms) pass_ms[i] = acc[i];
+    if (launches) launches[i] = cnt[i];
+  }
+  return RPCG_OK;
+}
+
+// Point the set-up SpMV node at x0 for this call.
+static cudaError_t set_x0(rpcg_matrix_t A, cudaGraphNode_t nd, cudaGraphExec_t e, const double* x) {
+  cudaKernelNodeParams p{};
+  cudaError_t err = cudaGraphKernelNodeGetParams(nd, &p);
+  if (err != cudaSuccess) return err;
+  CsrDev m = A->m;
+  const double* x0 = x;
+  double* w = A->w;
+  void* a[] = {&m, &x0, &w};
+  p.kernelParams = a;
+  return cudaGraphExecKernelNodeSetParams(e, nd, &p);
+}
+
+static rpcg_status alloc_dev(void** p, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e == cudaErrorMemoryAllocation) {
+    cudaGetLastError();
+    set_error("cudaMalloc of %zu bytes failed", bytes);
+    return RPCG_ERR_OOM;
+  }
+  if (e != cudaSuccess) {
+    set_error("cudaMalloc failed: %s", cudaGetErrorString(e));
+    return RPCG_ERR_CUDA;
+  }
+  return RPCG_OK;
+}
+
+__global__ void k_check_csr(int n, int nnz, const int* rowptr, const int* col, int* bad) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i <= n; i += gridDim.x * blockDim.x) {
+    const int v = rowptr[i];
+    if (v < 0 || v > nnz || (i == 0 && v != 0) || (i == n && v != nnz) || (i < n && rowptr[i + 1] < v)) atomicOr(bad, 1);
+  }
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nnz; k += gridDim.x * blockDim.x) {
+    const int c = col[k];
+    if (c < 0 || c >= n) atomicOr(bad, 2);
+  }
+}
+
+static void destroy_handle(rpcg_matrix_t A) {
+  if (!A) return;
+  for (auto& kv : A->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto& kv : A->graph_defs) cudaGraphDestroy(kv.second);
+  cudaFree(A->rowptr);
+  cudaFree(A->col);
+  cudaFree(A->val);
+  cudaFree(A->inv);
+  cudaFree(A->r);
+  cudaFree(A->d);
+  cudaFree(A->w);
+  cudaFree(A->bx);
+  cudaFree(A->args);
+  cudaFree(A->state);
+  cudaFree(A->scratch);
+  cudaFreeHost(A->h_args);
+  cudaFreeHost(A->h_state);
+  delete A;
+}
+
+}  // namespace rpcg
+
+using namespace rpcg;
+
+extern "C" {
+
+void rpcg_opts_default(rpcg_opts* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->tol = 1e-8;
+  o->max_iter = 1000;
+  o->fpe_size = 8;
+  o->fpe_strict = 0;
+}
+
+rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int32_t* rowptr, const int32_t* col,
+                        const double* val, int32_t ptr_kind, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(A_out != nullptr, "A_out is NULL");
+  *A_out = nullptr;
+  RPCG_CHECK_ARG(n >= 0 && nnz >= 0, "n and nnz must be non-negative");
+  RPCG_CHECK_ARG(rowptr != nullptr, "rowptr is NULL");
+  RPCG_CHECK_ARG(nnz == 0 || (col != nullptr && val != nullptr), "col or val is NULL");
+  RPCG_CHECK_ARG(ptr_kind == 0 || ptr_kind == 1, "ptr_kind must be 0 (host) or 1 (device)");
+  cudaStream_t s = (cudaStream_t)stream;
+  if (ptr_kind == 0 && (rowptr[0] != 0 || rowptr[n] != nnz)) {
+    set_error("rowptr[0] must be 0 and rowptr[n] must be nnz");
+    return RPCG_ERR_INVALID;
+  }
+  rpcg_matrix_t A = new rpcg_matrix_s();
+  cudaGetDevice(&A->device);
+  rpcg_status st = RPCG_OK;
+  const size_t vec = (size_t)(n > 0 ? n : 1) * sizeof(double);
+  const size_t nnz_pad = (size_t)nnz + 32;
+#define ALLOC(ptr, bytes)                                    \
+  do {                                                       \
+    st = alloc_dev((void**)&(ptr), (bytes));                 \
+    if (st != RPCG_OK) {                                     \
+      destroy_handle(A);                                     \
+      return st;                                             \
+    }                                                        \
+  } while (0)
+  ALLOC(A->rowptr, ((size_t)n + 1 + 8) * sizeof(int));
+  ALLOC(A->col, nnz_pad * sizeof(int));
+  ALLOC(A->val, nnz_pad * sizeof(double));
+  ALLOC(A->inv, vec);
+  ALLOC(A->r, vec);
+  ALLOC(A->d, vec);
+  ALLOC(A->w, vec);
+  ALLOC(A->bx, 2 * vec);
+  ALLOC(A->args, sizeof(SolveArgs));
+  ALLOC(A->state, sizeof(SolveState));
+  ALLOC(A->scratch, sizeof(PassScratch));
+#undef ALLOC
+  if (cudaMallocHost((void**)&A->h_args, sizeof(SolveArgs)) != cudaSuccess ||
+      cudaMallocHost((void**)&A->h_state, sizeof(SolveState)) != cudaSuccess) {
+    cudaGetLastError();
+    destroy_handle(A);
+    set_error("pinned host allocation failed");
+    return RPCG_ERR_OOM;
+  }
+  const cudaMemcpyKind kind = ptr_kind == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  cudaError_t e = cudaMemcpyAsync(A->rowptr, rowptr, ((size_t)n + 1) * sizeof(int), kind, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->col, col, (size_t)nnz * sizeof(int), kind, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->val, val, (size_t)nnz * sizeof(double), kind, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->col + nnz, 0, 32 * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->val + nnz, 0, 32 * sizeof(double), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->scratch, 0, offsetof(PassScratch, partials), s);
+  // validate the copied CSR on the device (monotone row pointers, columns in range)
+  if (e == cudaSuccess) {
+    int* bad = nullptr;
+    e = cudaMallocAsync((void**)&bad, sizeof(int), s);
+    int hbad = 0;
+    if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
+    if (e == cudaSuccess) {
+      int g = sm_count() * 4;
+      k_check_csr<<<g, 256, 0, s>>>(n, nnz, A->rowptr, A->col, bad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (bad) cudaFreeAsync(bad, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && hbad) {
+      destroy_handle(A);
+      set_error("invalid CSR (row pointers %s, column indices %s)", (hbad & 1) ? "bad" : "ok", (hbad & 2) ? "bad" : "ok");
+      return RPCG_ERR_INVALID;
+    }
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    set_error("rpcg_create: %s", cudaGetErrorString(e));
+    destroy_handle(A);
+    return RPCG_ERR_CUDA;
+  }
+  A->m.n = n;
+  A->m.nnz = nnz;
+  A->m.rowptr = A->rowptr;
+  A->m.col = A->col;
+  A->m.val = A->val;
+  *A_out = A;
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_destroy(rpcg_matrix_t A) {
+  clear_error();
+  if (!A) return RPCG_OK;
+  cudaDeviceSynchronize();
+  destroy_handle(A);
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_matrix_info(rpcg_matrix_t A, int32_t* n, int32_t* nnz) {
+  RPCG_CHECK_ARG(A != nullptr, "A is NULL");
+  if (n) *n = A->m.n;
+  if (nnz) *nnz = A->m.nnz;
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_spmv(rpcg_matrix_t A, const double* x, double* y, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(A != nullptr, "A is NULL");
+  RPCG_CHECK_ARG(A->m.n == 0 || (x && y), "x or y is NULL");
+  if (A->m.n == 0) return RPCG_OK;
+  constexpr int B = 256;
+  const size_t smem = spmv_smem<B>();
+  RPCG_CUDA_TRY(set_smem(k_spmv<B>, smem));
+  const int ntiles = (A->m.n + B - 1) / B;
+  int g = sm_count() * 2;
+  if (g > ntiles) g = ntiles;
+  k_spmv<B><<<g, B, smem, (cudaStream_t)stream>>>(A->m, x, y);
+  RPCG_CUDA_TRY(cudaGetLastError());
+  return RPCG_OK;
+}
+
+static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32_t v, const rpcg_opts* o,
+                              rpcg_result* res, cudaStream_t s, float* pass_ms = nullptr, int* launches = nullptr) {
+  rpcg_opts opt;
+  if (o) opt = *o;
+  else rpcg_opts_default(&opt);
+  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS || v == RPCG_FPE, "unknown variant");
+  RPCG_CHECK_ARG(opt.max_iter >= 0, "max_iter must be >= 0");
+  RPCG_CHECK_ARG(!(opt.tol < 0.0) && !std::isnan(opt.tol), "tol must be >= 0");
+  RPCG_CHECK_ARG(opt.fpe_size >= 1 && opt.fpe_size <= kFpeMax, "fpe_size must be 1..8");
+  RPCG_CHECK_ARG(opt.grid >= 0 && opt.grid <= kMaxPassGrid, "grid must be 0..4096");
+  const int block = pick_block(opt.block);
+  RPCG_CHECK_ARG(opt.block == 0 || opt.block == block, "block must be 0, 128, 256 or 512");
+  if (v == RPCG_FPE && opt.grid > 512) opt.grid = 512;
+  const int n = A->m.n;
+  if (n == 0) {
+    res->iterations = 0;
+    res->status = RPCG_OK;
+    res->relres = 0.0;
+    res->tau = 0.0;
+    res->fpe_inexact_count = 0;
+    if (opt.history) RPCG_CUDA_TRY(cudaMemsetAsync(opt.history, 0, sizeof(double), s));
+    RPCG_CUDA_TRY(cudaStreamSynchronize(s));
+    return RPCG_OK;
+  }
+  const bool eager = pass_ms != nullptr;
+  cudaGraphExec_t exec = nullptr;
+  if (!eager) {
+    rpcg_status st = get_graph(A, v, block, opt.grid, &exec);
+    if (st != RPCG_OK) return st;
+    RPCG_CUDA_TRY(set_x0(A, A->x0_nodes[GraphKey{v, block, opt.grid}], exec, x));
+  }
+  SolveArgs* ha = A->h_args;
+  ha->b = b;
+  ha->x = x;
+  ha->history = opt.history;
+  ha->tol = opt.tol;
+  ha->max_iter = opt.max_iter;
+  ha->fpe_size = opt.fpe_size;
+  ha->fpe_strict = opt.fpe_strict;
+  ha->variant = v;
+  ha->use_cond = eager ? 0 : 1;
+  RPCG_CUDA_TRY(cudaMemcpyAsync(A->args, ha, sizeof(SolveArgs), cudaMemcpyHostToDevice, s));
+  if (eager) {
+    rpcg_status st;
+#define RPCG_EAGER(VV, BB) st = run_eager<VV, BB>(A, opt.grid, x, s, pass_ms, launches)
+    if (block == 128) {
+      if (v == RPCG_PLAIN) RPCG_EAGER(RPCG_PLAIN, 128); else if (v == RPCG_EXBLAS) RPCG_EAGER(RPCG_EXBLAS, 128); else RPCG_EAGER(RPCG_FPE, 128);
+    } else if (block == 512) {
+      if (v == RPCG_PLAIN) RPCG_EAGER(RPCG_PLAIN, 512); else if (v == RPCG_EXBLAS) RPCG_EAGER(RPCG_EXBLAS, 512); else RPCG_EAGER(RPCG_FPE, 512);
+    } else {
+      if (v == RPCG_PLAIN) RPCG_EAGER(RPCG_PLAIN, 256); else if (v == RPCG_EXBLAS) RPCG_EAGER(RPCG_EXBLAS, 256); else RPCG_EAGER(RPCG_FPE, 256);
+    }
+#undef RPCG_EAGER
+    if (st != RPCG_OK) return st;
+  } else {
+    RPCG_CUDA_TRY(cudaGraphLaunch(exec, s));
+  }
+  RPCG_CUDA_TRY(cudaMemcpyAsync(A->h_state, A->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
+  RPCG_CUDA_TRY(cudaStreamSynchronize(s));
+  const SolveState& hs = *A->h_state;
+  if (hs.bzero) {
+    RPCG_CUDA_TRY(cudaMemsetAsync(x, 0, (size_t)n * sizeof(double), s));
+    RPCG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  int status = hs.status;
+  if (status == RPCG_OK) {
+    if (!(hs.rel < opt.tol)) status = RPCG_NOT_CONVERGED;
+    else if (v == RPCG_FPE && opt.fpe_strict && hs.fpe_inexact > 0) status = RPCG_FPE_INEXACT;
+  }
+  res->iterations = hs.iter;
+  res->status = status;
+  res->relres = hs.rel;
+  res->tau = hs.tau;
+  res->fpe_inexact_count = hs.fpe_inexact;
+  res->reserved = 0;
+  return (rpcg_status)status;
+}
+
+rpcg_status rpcg_solve(rpcg_matrix_t A, const double* b, double* x, int32_t v, const rpcg_opts* o, rpcg_result* res,
+                       void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(A != nullptr, "A is NULL");
+  RPCG_CHECK_ARG(res != nullptr, "res is NULL");
+  RPCG_CHECK_ARG(A->m.n == 0 || (b && x), "b or x is NULL");
+  return solve_impl(A, b, x, v, o, res, (cudaStream_t)stream);
+}
+
+rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double* b, double* x, int32_t v, const rpcg_opts* o,
+                                rpcg_result* res, float* pass_ms, int32_t* launches, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(A != nullptr, "A is NULL");
+  RPCG_CHECK_ARG(res != nullptr && pass_ms != nullptr, "res or pass_ms is NULL");
+  RPCG_CHECK_ARG(A->m.n == 0 || (b && x), "b or x is NULL");
+  for (int i = 0; i < 4; i++) {
+    pass_ms[i] = 0.f;
+    if (launches) launches[i] = 0;
+  }
+  return solve_impl(A, b, x, v, o, res, (cudaStream_t)stream, pass_ms, launches);
+}
+
+rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double* b_host, double* x_host, int32_t v, const rpcg_opts* o,
+                            rpcg_result* res, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(A != nullptr, "A is NULL");
+  RPCG_CHECK_ARG(res != nullptr, "res is NULL");
+  RPCG_CHECK_ARG(A->m.n == 0 || (b_host && x_host), "b or x is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bytes = (size_t)A->m.n * sizeof(double);
+  double* db = A->bx;
+  double* dx = A->bx + (A->m.n > 0 ? A->m.n : 1);
+  if (bytes) {
+    RPCG_CUDA_TRY(cudaMemcpyAsync(db, b_host, bytes, cudaMemcpyHostToDevice, s));
+    RPCG_CUDA_TRY(cudaMemcpyAsync(dx, x_host, bytes, cudaMemcpyHostToDevice, s));
+  }
+  rpcg_status st = solve_impl(A, db, dx, v, o, res, s);
+  if (st < 0 && st != RPCG_ERR_NOT_SPD && st != RPCG_ERR_NONFINITE) return st;
+  if (bytes) {
+    RPCG_CUDA_TRY(cudaMemcpyAsync(x_host, dx, bytes, cudaMemcpyDeviceToHost, s));
+    RPCG_CUDA_TRY(cudaStreamSynchronize(s));
+  }
+  return st;
+}
+
+}  // extern "C"

@@ -18,3 +18,27 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def rpcg():
+    """The CUDA library binding, built in-tree if needed."""
+    from paper_2005_07282_gb300 import build
+    build.build()
+    import paper_2005_07282_gb300 as P
+    P.lib()
+    return P
+
+
+@pytest.fixture(scope="session")
+def cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def bits(x):
+    """int64 view of float64 data (bit-exact comparison, NaN-safe)."""
+    import numpy as np
+    return np.ascontiguousarray(x, dtype=np.float64).view(np.int64)

@@ -1,0 +1,146 @@
+"""GPU parity of the three dot products against the CPU oracle (exact
+results compared bit for bit; element-by-element inputs shared through the
+seeded generators)."""
+import math
+import os
+import random
+
+import numpy as np
+import pytest
+
+import synth
+from conftest import bits
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+SIZES = [0, 1, 2, 3, 31, 257, 4097, 65537, 1000003]  # several tiles and ragged tails
+
+
+def _dev(x, cuda):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(cuda)
+
+
+def _exact_gpu(rpcg, a, b, cuda):
+    return rpcg.dot_exact(_dev(a, cuda), _dev(b, cuda)).item()
+
+
+def same(x, y):
+    return bits([x])[0] == bits([y])[0] or (math.isnan(x) and math.isnan(y))
+
+
+@pytest.mark.parametrize("fam", ["a", "b", "c8", "c24", "c40"])
+@pytest.mark.parametrize("n", SIZES)
+def test_dot_exact_families(rpcg, cuda, oracle_lib, fam, n):
+    if fam.startswith("c"):
+        if n < 4:
+            pytest.skip("family c needs n >= 4")
+        a, b = synth.dot_family_c(n, float("1e" + fam[1:]), synth.BASE_SEED + 1)
+    else:
+        a, b = getattr(synth, f"dot_family_{fam}")(n, synth.BASE_SEED + 1)
+    want = oracle_lib.dot_exact(a, b, nthreads=oracle_lib.default_threads())
+    assert same(_exact_gpu(rpcg, a, b, cuda), want)
+
+
+def test_dot_exact_golden(rpcg, cuda, oracle_lib):
+    for line in open(os.path.join(GOLDEN, "exact_dot_cases.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        a, b, _ = (part.split() for part in line.split(";"))
+        a = [float.fromhex(t) for t in a]
+        b = [float.fromhex(t) for t in b]
+        assert same(_exact_gpu(rpcg, a, b, cuda), oracle_lib.dot_exact(a, b)), line
+
+
+def _rand_double(rng, lo, hi):
+    e = rng.randint(lo, hi)
+    m = rng.getrandbits(52)
+    v = math.ldexp(m, -1074) if e < -1022 else math.ldexp((1 << 52) | m, e - 52)
+    return -v if rng.random() < 0.5 else v
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_dot_exact_extreme_exponents(rpcg, cuda, oracle_lib, seed):
+    """Subnormal operands, products far below 2^-1074 and near 2^2046."""
+    rng = random.Random(seed)
+    n = 5000
+    a = [_rand_double(rng, -1074, 1023) for _ in range(n)]
+    b = [_rand_double(rng, -1074, 1023 if seed % 2 else 0) for _ in range(n)]
+    assert same(_exact_gpu(rpcg, a, b, cuda), oracle_lib.dot_exact(a, b))
+
+
+def test_dot_exact_special_values(rpcg, cuda, oracle_lib):
+    n = 3000
+    a, b = synth.dot_family_a(n, 5)
+    for bad in (math.inf, -math.inf, math.nan):
+        a2 = a.copy()
+        a2[1234] = bad
+        assert math.isnan(_exact_gpu(rpcg, a2, b, cuda))
+    # exact cancellation is +0, n ones is n
+    x = synth.uniform_pm1(3, 4097)
+    assert same(_exact_gpu(rpcg, np.concatenate([x, -x]), np.concatenate([x, x]), cuda), 0.0)
+    assert _exact_gpu(rpcg, np.ones(100001), np.ones(100001), cuda) == 100001.0
+    # tiny negative values that round to zero keep their sign
+    assert same(_exact_gpu(rpcg, [-2.0 ** -600], [2.0 ** -500], cuda), oracle_lib.dot_exact([-2.0 ** -600], [2.0 ** -500]))
+
+
+def test_dot_exact_misaligned_and_strided_views(rpcg, cuda, oracle_lib):
+    import torch
+    a, b = synth.dot_family_b(20001, 8)
+    ta, tb = _dev(a, cuda), _dev(b, cuda)
+    for off in (1, 3):
+        va, vb = ta[off:], tb[:-off]
+        want = oracle_lib.dot_exact(a[off:], b[:-off])
+        assert same(rpcg.dot_exact(va, vb).item(), want)
+
+
+def test_dot_exact_order_independent(rpcg, cuda, oracle_lib):
+    a, b = synth.dot_family_c(200000, 1e30, 44)
+    v0 = _exact_gpu(rpcg, a, b, cuda)
+    perm = np.random.default_rng(1).permutation(a.size)
+    assert same(_exact_gpu(rpcg, a[perm], b[perm], cuda), v0)
+    assert same(v0, oracle_lib.dot_exact(a, b, nthreads=4))
+
+
+@pytest.mark.parametrize("fam", ["a", "c8", "c16", "c40"])
+@pytest.mark.parametrize("p", [2, 3, 8])
+def test_dot_fpe_equals_exact_when_flagged(rpcg, cuda, oracle_lib, fam, p):
+    n = 300001
+    if fam == "a":
+        a, b = synth.dot_family_a(n, 9)
+    else:
+        a, b = synth.dot_family_c(n, float("1e" + fam[1:]), 9)
+    v, ex = rpcg.dot_fpe(_dev(a, cuda), _dev(b, cuda), p=p)
+    want = oracle_lib.dot_exact(a, b, nthreads=4)
+    if ex.item():
+        assert same(v.item(), want)
+    if fam == "a" and p >= 3:
+        assert ex.item() == 1
+    if fam == "c40" and p == 2:
+        assert ex.item() == 0
+
+
+def test_dot_fpe_flag_cases(rpcg, cuda):
+    v, ex = rpcg.dot_fpe(_dev([2.0 ** -500, 1.0], cuda), _dev([2.0 ** -500, 1.0], cuda), p=8)
+    assert ex.item() == 0
+    v, ex = rpcg.dot_fpe(_dev([1.0, math.inf], cuda), _dev([1.0, 1.0], cuda), p=8)
+    assert ex.item() == 0 and math.isnan(v.item())
+    v, ex = rpcg.dot_fpe(_dev([], cuda), _dev([], cuda), p=8)
+    assert ex.item() == 1 and same(v.item(), 0.0)
+
+
+def test_dot_plain_close(rpcg, cuda, oracle_lib):
+    a, b = synth.dot_family_a(1000003, 12)
+    want = oracle_lib.dot_exact(a, b, nthreads=4)
+    got = rpcg.dot_plain(_dev(a, cuda), _dev(b, cuda)).item()
+    # fp64 error bound of a summation tree: n * u * sum|a_i b_i|
+    assert abs(got - want) <= 1e-16 * a.size * float(np.abs(a * b).sum())
+
+
+def test_dot_exact_repeat_is_deterministic(rpcg, cuda):
+    a, b = synth.dot_family_b(777777, 3)
+    ta, tb = _dev(a, cuda), _dev(b, cuda)
+    vals = {bits([rpcg.dot_exact(ta, tb).item()])[0] for _ in range(5)}
+    assert len(vals) == 1
