@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain/fpe/dot/e2e side measurements")
+    ap.add_argument("--eager", action="store_true",
+                    help="launch the solver's kernels one by one instead of the graph (for profilers)")
     return ap.parse_args()
 
 
@@ -213,6 +215,8 @@ def gpu_arm(args, rank, world, local_rank):
 
     def solve(variant, **kw):
         x.zero_()
+        if args.eager:
+            return M.solve_profiled(d_b, x, variant=variant, **{**opts, **kw})
         return M.solve(d_b, x, variant=variant, **{**opts, **kw})
 
     # ---- warm-up (builds and caches the graphs)
@@ -350,7 +354,8 @@ def gpu_arm(args, rank, world, local_rank):
                            "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
                            "solve_status": status, "step": "one complete solve from x0 = 0",
                            "l2": "inputs larger than L2 (CSR 5.46 GB streamed every iteration)",
-                           "parallelism": f"replicas x{world}"},
+                           "parallelism": f"replicas x{world}",
+                           "launch": "eager (kernel by kernel)" if args.eager else "CUDA graph, device-side loop"},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, **extras}
         print(json.dumps(line), flush=True)

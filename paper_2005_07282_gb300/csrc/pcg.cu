@@ -15,6 +15,7 @@
 // This merges S1 with S2 and S4 with S5 and S6 -- the task overlap of
 // Sec. 3.3 turned into kernel fusion.  The loop body is the child graph of a
 // conditional while node, so no host round trip happens per iteration.
+#include <algorithm>
 #include <climits>
 #include <cmath>
 #include <cstring>
@@ -29,7 +30,6 @@
 namespace rpcg {
 
 constexpr int kMaxPassGrid = 4096;
-constexpr int kSpmvCapPerRow = 32;  // staged nnz per row of a tile (on average)
 
 // Per-solve arguments, written by the host before every launch of the graph.
 struct SolveArgs {
@@ -59,12 +59,24 @@ struct PassScratch {
   double fpe[3][512][kFpeMax];          // fpe: CTA expansions (grid <= 512 for fpe)
 };
 
-struct CsrDev {
+// Device matrix.  The handle stores A in SELL-32 form: rows are grouped
+// in slices of 32 consecutive rows, and slice s keeps the k-th entry of its
+// 32 rows contiguously at sptr[s] + 32 k + lane, for k below the longest row
+// of the slice (shorter rows are padded; padded entries are never used).
+// Each row keeps its CSR storage order, so the k-th FMA of a row is the
+// same as in CSR.  A warp (32 consecutive rows) then reads 256 contiguous
+// bytes of values and 128 of columns per step, straight from HBM.
+struct MatDev {
   int n, nnz;
-  const int* rowptr;
-  const int* col;
-  const double* val;
+  const int* rowptr;     // CSR row pointers (row lengths), n + 1
+  const long long* sptr; // slice offsets, n / 32 + 1 (rounded up)
+  const double* val;     // SELL-32 values
+  const int* col;        // SELL-32 columns
 };
+
+__device__ __forceinline__ long long sell_index(const MatDev& m, int row, int k) {
+  return __ldg(m.sptr + (row >> 5)) + 32ll * k + (row & 31);
+}
 
 // ------------------------------------------------------------------ reducers
 
@@ -338,13 +350,15 @@ __global__ void k_init_state(SolveState* st, int n) {
 
 // Jacobi preconditioner (Sec. 3.1, Sec. 4.3): inv_i = RN(1 / a_ii).  Rows
 // without a positive finite diagonal are recorded (lowest index wins).
-__global__ void k_inv_diag(CsrDev m, double* inv, SolveState* st) {
+__global__ void k_inv_diag(MatDev m, double* inv, SolveState* st) {
   for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < m.n; i += gridDim.x * blockDim.x) {
     double aii = 0.0;
     bool found = false;
-    for (int k = m.rowptr[i]; k < m.rowptr[i + 1]; k++) {
-      if (m.col[k] == i) {
-        aii = m.val[k];
+    const int len = m.rowptr[i + 1] - m.rowptr[i];
+    const long long base = sell_index(m, i, 0);
+    for (int k = 0; k < len; k++) {
+      if (m.col[base + 32ll * k] == i) {
+        aii = m.val[base + 32ll * k];
         found = true;
       }
     }
@@ -357,81 +371,85 @@ __global__ void k_inv_diag(CsrDev m, double* inv, SolveState* st) {
   }
 }
 
-// One tile of BLOCK rows of y = A x, rows summed left to right with fma
-// from +0 (Sec. 4.3).  The tile's CSR slab is staged in shared memory with
-// coalesced loads when it fits; otherwise rows read global memory directly.
-template <int BLOCK>
-__device__ __forceinline__ double spmv_tile(const CsrDev& m, const double* __restrict__ x, int tile, double* s_val,
-                                            int* s_col, int cap, int& row) {
-  const int r0 = tile * BLOCK;
-  const int r1 = min(r0 + BLOCK, m.n);
-  const int k0 = __ldg(m.rowptr + r0);
-  const int k1 = __ldg(m.rowptr + r1);
-  const int cnt = k1 - k0;
-  const bool staged = cnt <= cap;
-  __syncthreads();  // the previous tile is done with the slab
-  if (staged) {
-    for (int k = threadIdx.x; k < cnt; k += BLOCK) {
-      s_val[k] = __ldcs(m.val + k0 + k);
-      s_col[k] = __ldcs(m.col + k0 + k);
+// ---- SpMV: y = A x, each row summed left to right with fma from +0 (Sec. 4.3).
+//
+// One thread per row, a warp per 32-row slice, CTAs persistent over the
+// slices.  The matrix stream is read with coalesced streaming loads; the
+// gathers x[col] go through L1/L2 (stencil locality).  The loads of the
+// next 8 entries are issued before the FMAs of the current 8.
+__device__ __forceinline__ double sell_row(const MatDev& m, int row, const double* __restrict__ x) {
+  constexpr int U = 8;
+  const int len = __ldg(m.rowptr + row + 1) - __ldg(m.rowptr + row);
+  const long long base = sell_index(m, row, 0);
+  const double* __restrict__ vp = m.val + base;
+  const int* __restrict__ cp = m.col + base;
+  double acc = 0.0;
+  double xa[U], va[U];
+#pragma unroll
+  for (int j = 0; j < U; j++) {
+    xa[j] = 0.0;
+    va[j] = 0.0;
+    if (j < len) {
+      va[j] = __ldcs(vp + 32 * j);
+      xa[j] = __ldg(x + __ldcs(cp + 32 * j));
     }
   }
-  __syncthreads();
-  row = r0 + threadIdx.x;
-  double acc = 0.0;
-  if (row < m.n) {
-    const int a = __ldg(m.rowptr + row), e = __ldg(m.rowptr + row + 1);
-    if (staged) {
-      for (int k = a - k0; k < e - k0; k++) acc = __fma_rn(s_val[k], __ldg(x + s_col[k]), acc);
-    } else {
-      for (int k = a; k < e; k++) acc = __fma_rn(__ldg(m.val + k), __ldg(x + __ldg(m.col + k)), acc);
+  for (int k = 0; k < len; k += U) {
+    double xb[U], vb[U];
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      const int kk = k + U + j;
+      xb[j] = 0.0;
+      vb[j] = 0.0;
+      if (kk < len) {
+        vb[j] = __ldcs(vp + 32ll * kk);
+        xb[j] = __ldg(x + __ldcs(cp + 32ll * kk));
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < U; j++)
+      if (k + j < len) acc = __fma_rn(va[j], xa[j], acc);
+#pragma unroll
+    for (int j = 0; j < U; j++) {
+      xa[j] = xb[j];
+      va[j] = vb[j];
     }
   }
   return acc;
 }
 
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_spmv(CsrDev m, const double* __restrict__ x, double* __restrict__ y) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int cap = BLOCK * kSpmvCapPerRow;
-  double* s_val = reinterpret_cast<double*>(smem);
-  int* s_col = reinterpret_cast<int*>(s_val + cap);
-  const int ntiles = (m.n + BLOCK - 1) / BLOCK;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int row;
-    const double v = spmv_tile<BLOCK>(m, x, tile, s_val, s_col, cap, row);
-    if (row < m.n) y[row] = v;
-  }
+__global__ void __launch_bounds__(BLOCK) k_spmv(MatDev m, const double* __restrict__ x, double* __restrict__ y) {
+  for (int row = blockIdx.x * BLOCK + threadIdx.x; row < m.n; row += gridDim.x * BLOCK) y[row] = sell_row(m, row, x);
 }
 
 // Pass A: S1 + S2.
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_pass_a(CsrDev m, const double* __restrict__ d, double* __restrict__ w,
+__global__ void __launch_bounds__(BLOCK) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
                                                   PassScratch* ws, SolveState* st, const SolveArgs* args,
                                                   cudaGraphConditionalHandle cond) {
   extern __shared__ __align__(16) unsigned char smem[];
-  const int cap = BLOCK * kSpmvCapPerRow;
-  double* s_val = reinterpret_cast<double*>(smem);
-  int* s_col = reinterpret_cast<int*>(s_val + cap);
   unsigned long long* sacc;
-  FinalScratch* fs = red_carve<V, 1>(reinterpret_cast<unsigned char*>(s_col + cap), sacc);
-  if (st->status != 0) return;
-  const int p = args->fpe_size;
-  if constexpr (V == RPCG_EXBLAS) {
-    smem_acc_zero(sacc);
+  FinalScratch* fs = red_carve<V, 1>(smem, sacc);
+  if (st->status != 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) stop_loop(st, args, cond);
+    return;
   }
+  const int p = args->fpe_size;
+  if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc);
+  __syncthreads();
   Reducer<V, 1> R;
   red_init(R);
-  const int ntiles = (m.n + BLOCK - 1) / BLOCK;
-  for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-    int row;
-    const double v = spmv_tile<BLOCK>(m, d, tile, s_val, s_col, cap, row);
-    if (row < m.n) {
-      w[row] = v;
-      red_add(R, sacc, 0, __ldg(d + row), v, p);
-    }
+  for (int row = blockIdx.x * BLOCK + threadIdx.x; row < m.n; row += gridDim.x * BLOCK) {
+    const double v = sell_row(m, row, d);
+    w[row] = v;
+    red_add(R, sacc, 0, __ldg(d + row), v, p);
   }
   if (red_finish<V, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
+    if (st->status != 0) {
+      stop_loop(st, args, cond);
+      return;
+    }
     if (V == RPCG_FPE && fs->lost[0]) {
       st->fpe_inexact += 1;
       if (!args->fpe_strict) {
@@ -452,7 +470,10 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* sacc;
   FinalScratch* fs = red_carve<V, 2>(smem, sacc);
-  if (st->status != 0 || st->redo) return;
+  if (st->status != 0 || st->redo) {
+    if (st->status != 0 && blockIdx.x == 0 && threadIdx.x == 0) stop_loop(st, args, cond);
+    return;
+  }
   const int p = args->fpe_size;
   double* __restrict__ x = args->x;
   const double rho = st->rho, nrho = -st->rho;
@@ -543,7 +564,7 @@ __global__ void __launch_bounds__(BLOCK) k_redo_b(int n, const double* __restric
 // relres0 and the initial loop condition.  The set-up dots are always exact
 // (plain for the plain variant).
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_setup(CsrDev m, const double* __restrict__ q, const double* __restrict__ inv,
+__global__ void __launch_bounds__(BLOCK) k_setup(MatDev m, const double* __restrict__ q, const double* __restrict__ inv,
                                                  double* __restrict__ r, double* __restrict__ d, PassScratch* ws,
                                                  SolveState* st, const SolveArgs* args,
                                                  cudaGraphConditionalHandle cond) {
@@ -573,8 +594,10 @@ __global__ void __launch_bounds__(BLOCK) k_setup(CsrDev m, const double* __restr
       // the lowest-index row without a positive finite diagonal decides
       const int i = st->bad_row;
       double aii = 0.0;
-      for (int k = m.rowptr[i]; k < m.rowptr[i + 1]; k++)
-        if (m.col[k] == i) aii = m.val[k];
+      const int len = m.rowptr[i + 1] - m.rowptr[i];
+      const long long base = sell_index(m, i, 0);
+      for (int k = 0; k < len; k++)
+        if (m.col[base + 32ll * k] == i) aii = m.val[base + 32ll * k];
       st->status = isfinite(aii) ? RPCG_ERR_NOT_SPD : RPCG_ERR_NONFINITE;
       stop_loop(st, args, cond);
       return;
@@ -617,10 +640,11 @@ struct GraphKey {
 }  // namespace rpcg
 
 struct rpcg_matrix_s {
-  rpcg::CsrDev m{};
+  rpcg::MatDev m{};
   int* rowptr = nullptr;
-  int* col = nullptr;
-  double* val = nullptr;
+  long long* sptr = nullptr;  // SELL-32 slice offsets
+  int* col = nullptr;         // SELL-32 columns
+  double* val = nullptr;      // SELL-32 values
   double* inv = nullptr;
   double* r = nullptr;
   double* d = nullptr;
@@ -643,7 +667,7 @@ static int pick_block(int b) { return (b == 128 || b == 256 || b == 512) ? b : 2
 
 template <int BLOCK>
 static size_t spmv_smem() {
-  return (size_t)BLOCK * kSpmvCapPerRow * (sizeof(double) + sizeof(int));
+  return 0;
 }
 
 template <int V, int NACC>
@@ -679,14 +703,22 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
   const int sms = sm_count();
   const int ntiles = (n + BLOCK - 1) / BLOCK;
   int grid_stream = grid > 0 ? grid : sms * (BLOCK >= 512 ? 2 : 4);
-  int grid_tiles = grid > 0 ? grid : sms * 2;
+  // persistent tile grid: as many CTAs as can be resident at once
+  int occ = 1;
+  {
+    const size_t sm_a = pass_smem<V, 1>();
+    RPCG_CUDA_TRY(set_smem(k_pass_a<V, BLOCK>, sm_a));
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_pass_a<V, BLOCK>, BLOCK, sm_a) != cudaSuccess || occ < 1)
+      occ = 1;
+  }
+  int grid_tiles = grid > 0 ? grid : sms * occ;
   if (V == RPCG_FPE) {
     if (grid_stream > 512) grid_stream = 512;
     if (grid_tiles > 512) grid_tiles = 512;
   }
   if (grid_stream > kMaxPassGrid) grid_stream = kMaxPassGrid;
   if (grid_tiles > kMaxPassGrid) grid_tiles = kMaxPassGrid;
-  if (grid_tiles > ntiles) grid_tiles = ntiles > 0 ? ntiles : 1;
+  if (grid_tiles > ntiles) grid_tiles = ntiles > 0 ? ntiles : 1;  // ntiles: CTAs of BLOCK rows
   const int grid_elem_cap = (n + BLOCK - 1) / BLOCK;
   if (grid_stream > grid_elem_cap) grid_stream = grid_elem_cap > 0 ? grid_elem_cap : 1;
   const int grid_small = (n + BLOCK - 1) / BLOCK > 0 ? ((n + BLOCK - 1) / BLOCK < sms * 8 ? (n + BLOCK - 1) / BLOCK : sms * 8) : 1;
@@ -694,7 +726,7 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
   c->grid_tiles = grid_tiles;
   c->grid_small = grid_small;
   c->smem_spmv = spmv_smem<BLOCK>();
-  c->smem_a = c->smem_spmv + pass_smem<V, 1>();
+  c->smem_a = pass_smem<V, 1>();
   c->smem_b = pass_smem<V, 2>();
   c->smem_s = pass_smem<(V == RPCG_PLAIN ? RPCG_PLAIN : RPCG_EXBLAS), 3>();
   c->smem_ra = pass_smem<RPCG_EXBLAS, 1>();
@@ -712,7 +744,7 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
 template <int V, int BLOCK>
 static rpcg_status build_graph(rpcg_matrix_t A, int grid, cudaGraph_t* out_graph, cudaGraphExec_t* out_exec,
                                cudaGraphNode_t* out_x0_node) {
-  CsrDev m = A->m;
+  MatDev m = A->m;
   int n = m.n;
   LaunchCfg c;
   rpcg_status cs = launch_cfg<V, BLOCK>(n, grid, &c);
@@ -828,7 +860,7 @@ static rpcg_status get_graph(rpcg_matrix_t A, int v, int block, int grid, cudaGr
 template <int V, int BLOCK>
 static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaStream_t s, float* pass_ms,
                              int* launches) {
-  CsrDev m = A->m;
+  MatDev m = A->m;
   const int n = m.n;
   LaunchCfg c;
   rpcg_status cs = launch_cfg<V, BLOCK>(n, grid, &c);
@@ -901,7 +933,7 @@ static cudaError_t set_x0(rpcg_matrix_t A, cudaGraphNode_t nd, cudaGraphExec_t e
   cudaKernelNodeParams p{};
   cudaError_t err = cudaGraphKernelNodeGetParams(nd, &p);
   if (err != cudaSuccess) return err;
-  CsrDev m = A->m;
+  MatDev m = A->m;
   const double* x0 = x;
   double* w = A->w;
   void* a[] = {&m, &x0, &w};
@@ -935,11 +967,27 @@ __global__ void k_check_csr(int n, int nnz, const int* rowptr, const int* col, i
   }
 }
 
+// Scatter CSR rows into the SELL-32 layout (entry k of row i at
+// sptr[i / 32] + 32 k + i % 32), keeping each row's storage order.
+__global__ void k_csr_to_sell(int n, const int* __restrict__ rowptr, const int* __restrict__ ccol,
+                              const double* __restrict__ cval, const long long* __restrict__ sptr, int* scol,
+                              double* sval) {
+  for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const int a = rowptr[i], e = rowptr[i + 1];
+    const long long base = sptr[i >> 5] + (i & 31);
+    for (int k = 0; k < e - a; k++) {
+      scol[base + 32ll * k] = ccol[a + k];
+      sval[base + 32ll * k] = cval[a + k];
+    }
+  }
+}
+
 static void destroy_handle(rpcg_matrix_t A) {
   if (!A) return;
   for (auto& kv : A->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : A->graph_defs) cudaGraphDestroy(kv.second);
   cudaFree(A->rowptr);
+  cudaFree(A->sptr);
   cudaFree(A->col);
   cudaFree(A->val);
   cudaFree(A->inv);
@@ -988,7 +1036,6 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
   cudaGetDevice(&A->device);
   rpcg_status st = RPCG_OK;
   const size_t vec = (size_t)(n > 0 ? n : 1) * sizeof(double);
-  const size_t nnz_pad = (size_t)nnz + 32;
 #define ALLOC(ptr, bytes)                                    \
   do {                                                       \
     st = alloc_dev((void**)&(ptr), (bytes));                 \
@@ -998,8 +1045,6 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
     }                                                        \
   } while (0)
   ALLOC(A->rowptr, ((size_t)n + 1 + 8) * sizeof(int));
-  ALLOC(A->col, nnz_pad * sizeof(int));
-  ALLOC(A->val, nnz_pad * sizeof(double));
   ALLOC(A->inv, vec);
   ALLOC(A->r, vec);
   ALLOC(A->d, vec);
@@ -1008,7 +1053,6 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
   ALLOC(A->args, sizeof(SolveArgs));
   ALLOC(A->state, sizeof(SolveState));
   ALLOC(A->scratch, sizeof(PassScratch));
-#undef ALLOC
   if (cudaMallocHost((void**)&A->h_args, sizeof(SolveArgs)) != cudaSuccess ||
       cudaMallocHost((void**)&A->h_state, sizeof(SolveState)) != cudaSuccess) {
     cudaGetLastError();
@@ -1016,14 +1060,26 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
     set_error("pinned host allocation failed");
     return RPCG_ERR_OOM;
   }
+  // 1. the CSR arrays into temporary device buffers
+  int* ccol = nullptr;
+  double* cval = nullptr;
+  auto free_tmp = [&]() {
+    cudaFree(ccol);
+    cudaFree(cval);
+  };
+  st = alloc_dev((void**)&ccol, (size_t)(nnz > 0 ? nnz : 1) * sizeof(int));
+  if (st == RPCG_OK) st = alloc_dev((void**)&cval, (size_t)(nnz > 0 ? nnz : 1) * sizeof(double));
+  if (st != RPCG_OK) {
+    free_tmp();
+    destroy_handle(A);
+    return st;
+  }
   const cudaMemcpyKind kind = ptr_kind == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
   cudaError_t e = cudaMemcpyAsync(A->rowptr, rowptr, ((size_t)n + 1) * sizeof(int), kind, s);
-  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->col, col, (size_t)nnz * sizeof(int), kind, s);
-  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(A->val, val, (size_t)nnz * sizeof(double), kind, s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(A->col + nnz, 0, 32 * sizeof(int), s);
-  if (e == cudaSuccess) e = cudaMemsetAsync(A->val + nnz, 0, 32 * sizeof(double), s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(ccol, col, (size_t)nnz * sizeof(int), kind, s);
+  if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(cval, val, (size_t)nnz * sizeof(double), kind, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(A->scratch, 0, offsetof(PassScratch, partials), s);
-  // validate the copied CSR on the device (monotone row pointers, columns in range)
+  // 2. validate on the device (monotone row pointers, columns in range)
   if (e == cudaSuccess) {
     int* bad = nullptr;
     e = cudaMallocAsync((void**)&bad, sizeof(int), s);
@@ -1031,19 +1087,59 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
     if (e == cudaSuccess) e = cudaMemsetAsync(bad, 0, sizeof(int), s);
     if (e == cudaSuccess) {
       int g = sm_count() * 4;
-      k_check_csr<<<g, 256, 0, s>>>(n, nnz, A->rowptr, A->col, bad);
+      k_check_csr<<<g, 256, 0, s>>>(n, nnz, A->rowptr, ccol, bad);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
     if (bad) cudaFreeAsync(bad, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess && hbad) {
+      free_tmp();
       destroy_handle(A);
       set_error("invalid CSR (row pointers %s, column indices %s)", (hbad & 1) ? "bad" : "ok", (hbad & 2) ? "bad" : "ok");
       return RPCG_ERR_INVALID;
     }
   }
+  // 3. SELL-32 slice offsets on the host from the (now validated) row pointers
+  const int nslices = (n + 31) / 32;
+  std::vector<long long> hsptr((size_t)nslices + 1, 0);
+  if (e == cudaSuccess) {
+    std::vector<int> hrp;
+    const int* rp = rowptr;
+    if (ptr_kind == 1) {
+      hrp.resize((size_t)n + 1);
+      e = cudaMemcpyAsync(hrp.data(), A->rowptr, ((size_t)n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      rp = hrp.data();
+    }
+    for (int sl = 0; sl < nslices && e == cudaSuccess; sl++) {
+      int len = 0;
+      const int r1 = std::min(n, 32 * sl + 32);
+      for (int i = 32 * sl; i < r1; i++) len = std::max(len, rp[i + 1] - rp[i]);
+      hsptr[sl + 1] = hsptr[sl] + 32ll * len;
+    }
+  }
+  const long long total = hsptr[nslices];
+  if (e == cudaSuccess) {
+    st = alloc_dev((void**)&A->sptr, ((size_t)nslices + 1) * sizeof(long long));
+    if (st == RPCG_OK) st = alloc_dev((void**)&A->col, ((size_t)total + 32) * sizeof(int));
+    if (st == RPCG_OK) st = alloc_dev((void**)&A->val, ((size_t)total + 32) * sizeof(double));
+    if (st != RPCG_OK) {
+      free_tmp();
+      destroy_handle(A);
+      return st;
+    }
+    e = cudaMemcpyAsync(A->sptr, hsptr.data(), ((size_t)nslices + 1) * sizeof(long long), cudaMemcpyHostToDevice, s);
+  }
+  // 4. scatter into SELL-32 (padding: column 0, value 0; never used)
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->col, 0, ((size_t)total + 32) * sizeof(int), s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(A->val, 0, ((size_t)total + 32) * sizeof(double), s);
+  if (e == cudaSuccess && n > 0) {
+    k_csr_to_sell<<<sm_count() * 8, 256, 0, s>>>(n, A->rowptr, ccol, cval, A->sptr, A->col, A->val);
+    e = cudaGetLastError();
+  }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  free_tmp();
   if (e != cudaSuccess) {
     set_error("rpcg_create: %s", cudaGetErrorString(e));
     destroy_handle(A);
@@ -1052,6 +1148,7 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
   A->m.n = n;
   A->m.nnz = nnz;
   A->m.rowptr = A->rowptr;
+  A->m.sptr = A->sptr;
   A->m.col = A->col;
   A->m.val = A->val;
   *A_out = A;
@@ -1082,7 +1179,9 @@ rpcg_status rpcg_spmv(rpcg_matrix_t A, const double* x, double* y, void* stream)
   const size_t smem = spmv_smem<B>();
   RPCG_CUDA_TRY(set_smem(k_spmv<B>, smem));
   const int ntiles = (A->m.n + B - 1) / B;
-  int g = sm_count() * 2;
+  int occ = 1;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_spmv<B>, B, smem) != cudaSuccess || occ < 1) occ = 1;
+  int g = sm_count() * occ;
   if (g > ntiles) g = ntiles;
   k_spmv<B><<<g, B, smem, (cudaStream_t)stream>>>(A->m, x, y);
   RPCG_CUDA_TRY(cudaGetLastError());
