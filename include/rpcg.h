@@ -139,6 +139,25 @@ rpcg_status rpcg_spmv(rpcg_matrix_t A, const double *x, double *y, void *stream)
 rpcg_status rpcg_dot_exact(int64_t n, const double *a, const double *b, double *out, void *stream);
 
 /*
+ * rpcg_dot_exact_noalloc -- the same exact dot as rpcg_dot_exact (same
+ * kernel, same result bits), for callers that cannot have the library
+ * allocate device memory: e.g. a framework whose own allocator already
+ * holds all of the GPU's memory, or a time-critical loop where an
+ * allocation and the synchronisation it may cause are not acceptable.  The
+ * paper has no counterpart; this is a deployment variant of Sec. 4.1's dot.
+ *   n         0 <= n <= 2^30 (larger n returns RPCG_ERR_INVALID).
+ *   a, b      device arrays of n doubles; out: device pointer to one double.
+ * It allocates nothing: its scratch is one fixed 64 KiB array inside the
+ * library, which every GPU that loads the library keeps until the process
+ * exits.  The first call on each device looks up that array's device
+ * address with the device current; make that first call before any stream
+ * capture.  All calls on a device share the one array: calls that may
+ * overlap on the GPU (on different streams without ordering between them)
+ * race and give wrong results; serialise them.  Asynchronous.
+ */
+rpcg_status rpcg_dot_exact_noalloc(int64_t n, const double *a, const double *b, double *out, void *stream);
+
+/*
  * rpcg_dot_fpe -- FPE dot of Sec. 4.2 / Listing 2: each thread keeps a
  * result expansion and an error expansion of p terms (Alg. 4 with the early
  * exit, fed by Alg. 2's product and error), the expansions are merged with

@@ -27,7 +27,7 @@ VARIANTS = {"plain": PLAIN, "exblas": EXBLAS, "fpe": FPE}
 EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
-    "rpcg_solve_host", "rpcg_solve_profiled",
+    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc",
 ]
 
 
@@ -75,6 +75,7 @@ def lib():
         L.rpcg_spmv.argtypes = [P, P, P, P]
         L.rpcg_dot_exact.argtypes = [i64, P, P, P, P]
         L.rpcg_dot_fpe.argtypes = [i64, P, P, i32, P, P, P]
+        L.rpcg_dot_exact_noalloc.argtypes = [i64, P, P, P, P]
         L.rpcg_dot_plain.argtypes = [i64, P, P, P, P]
         L.rpcg_solve.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
         L.rpcg_solve_host.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
@@ -121,6 +122,16 @@ def dot_exact(a, b, out=None, stream=None):
     out = torch.empty((), dtype=torch.float64, device=a.device) if out is None else out
     _check(lib().rpcg_dot_exact(a.numel(), _dptr(a), _dptr(b), ctypes.c_void_p(out.data_ptr()), _stream(stream)),
            "rpcg_dot_exact")
+    return out
+
+
+def dot_exact_noalloc(a, b, out=None, stream=None):
+    """rpcg_dot_exact_noalloc: the exact dot using the library's fixed
+    scratch array instead of allocating (see include/rpcg.h)."""
+    import torch
+    out = torch.empty((), dtype=torch.float64, device=a.device) if out is None else out
+    _check(lib().rpcg_dot_exact_noalloc(a.numel(), _dptr(a), _dptr(b), ctypes.c_void_p(out.data_ptr()),
+                                        _stream(stream)), "rpcg_dot_exact_noalloc")
     return out
 
 

@@ -2,6 +2,7 @@
 // flag, and the plain FP64 baseline; plus the library-wide host helpers.
 #include <cmath>
 #include <cstring>
+#include <mutex>
 
 #include "device.cuh"
 #include "host.h"
@@ -296,3 +297,74 @@ rpcg_status rpcg_dot_plain(int64_t n, const double* a, const double* b, double* 
 }
 
 }  // extern "C"
+
+// ------------------------------------------------------------------ exact dot without allocation
+//
+// Some callers cannot let a library allocate device memory: for example a
+// framework whose caching allocator has already reserved all of the GPU's
+// memory for itself, or a time-critical loop where an allocation (and the
+// device synchronisation that cudaMalloc may imply) is not acceptable.  For
+// them rpcg_dot_exact_noalloc runs the same exact-dot kernel as
+// rpcg_dot_exact, but its scratch is the fixed array below, which every GPU
+// that loads this library holds until the process exits.
+
+namespace rpcg {
+
+// Capacity of the fixed scratch: room for one DotScratch (about 34 KiB).
+constexpr size_t kNoAllocScratchBytes = 64 * 1024;
+static_assert(sizeof(DotScratch) <= kNoAllocScratchBytes, "DotScratch must fit the fixed scratch array");
+
+// Largest n accepted: the digit headroom of the long accumulator.
+constexpr int64_t kNoAllocMaxN = int64_t(1) << 30;
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+// Device address of g_noalloc_scratch per device, looked up once per device
+// (in host code the array's name is only a stand-in, not a device address).
+static std::mutex g_noalloc_mutex;
+static void* g_noalloc_addr[64] = {nullptr};
+
+static rpcg_status noalloc_scratch(void** out) {
+  int dev = 0;
+  RPCG_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 0 || dev >= 64) {
+    set_error("rpcg_dot_exact_noalloc: device index %d out of range", dev);
+    return RPCG_ERR_INVALID;
+  }
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // device `dev` is current here
+    if (e != cudaSuccess || p == nullptr) {
+      set_error("rpcg_dot_exact_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+      return RPCG_ERR_CUDA;
+    }
+    g_noalloc_addr[dev] = p;
+  }
+  *out = g_noalloc_addr[dev];
+  return RPCG_OK;
+}
+
+}  // namespace rpcg
+
+extern "C" rpcg_status rpcg_dot_exact_noalloc(int64_t n, const double* a, const double* b, double* out,
+                                              void* stream) {
+  clear_error();
+  if (n < 0 || n > kNoAllocMaxN) {
+    set_error("rpcg_dot_exact_noalloc: n = %lld is outside [0, 2^30], the largest size it accepts", (long long)n);
+    return RPCG_ERR_INVALID;
+  }
+  RPCG_CHECK_ARG(out != nullptr, "out is NULL");
+  RPCG_CHECK_ARG(n == 0 || (a != nullptr && b != nullptr), "a or b is NULL");
+  void* scratch = nullptr;
+  const rpcg_status st = noalloc_scratch(&scratch);
+  if (st != RPCG_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  DotScratch* ws = static_cast<DotScratch*>(scratch);
+  // the array keeps the previous call's contents: clear the part the kernel
+  // expects to start at zero (accumulator digits, arrival counter, flags)
+  RPCG_CUDA_TRY(cudaMemsetAsync(ws, 0, kDotScratchHeader, s));
+  k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
+  RPCG_CUDA_TRY(cudaGetLastError());
+  return RPCG_OK;
+}
