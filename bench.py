@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain/fpe/dot/e2e side measurements")
+    ap.add_argument("--dot-only", type=int, default=0, metavar="LOG2N",
+                    help="only time the exact, fpe and plain dots on 2^LOG2N U[-1,1] pairs")
     ap.add_argument("--eager", action="store_true",
                     help="launch the solver's kernels one by one instead of the graph (for profilers)")
     return ap.parse_args()
@@ -361,8 +363,43 @@ def gpu_arm(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def dot_arm(args):
+    """--dot-only: the three dot products on 2^k U[-1,1] pairs (16 B per element)."""
+    import torch
+
+    import paper_2005_07282_gb300 as P
+    from paper_2005_07282_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    n = 1 << args.dot_only
+    base = min(n, 1 << 24)
+    a0, b0 = synth.dot_family_a(base, synth.BASE_SEED + 1)
+    da = torch.from_numpy(a0).to(dev).repeat(n // base)
+    db = torch.from_numpy(b0).to(dev).repeat(n // base)
+    peak, kind = hbm_peak()
+    res = {}
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for name, fn in (("exact", lambda: P.dot_exact(da, db)), ("fpe", lambda: P.dot_fpe(da, db)),
+                     ("plain", lambda: P.dot_plain(da, db))):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0.record()
+        for _ in range(args.steps):
+            fn()
+        e1.record()
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        res[name] = {"ms": ms, "gbs": 16 * n / (ms * 1e-3) / 1e9, "frac": 16 * n / (ms * 1e-3) / 1e9 / peak}
+    print(json.dumps({"workload": f"dot U[-1,1] n=2^{args.dot_only}", "peak_gbs": peak, "peak_kind": kind,
+                      "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
+
+
 def main():
     args = parse()
+    if args.dot_only:
+        dot_arm(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     local_rank = int(os.environ.get("LOCAL_RANK", "0"))
