@@ -72,6 +72,13 @@ def workload(side):
     return A, xt
 
 
+# DRAM traffic of one pass-A launch over its algorithmic bytes, from the ncu
+# capture summarised in profiles/k_pass_a_p27_128.md (dram read + write of the
+# 128^3 case / its algorithmic bytes); the kernel streams every matrix entry
+# once, so the full-size launch's traffic is this ratio times its bytes.
+PASS_A_TRAFFIC_RATIO = 701.7 / 710.9
+
+
 def pass_a_bytes(n, nnz):
     """Algorithmic bytes of one pass-A launch: CSR stream, d read once, w written once."""
     return 12 * nnz + 4 * (n + 1) + 8 * n + 8 * n
@@ -286,7 +293,9 @@ def gpu_arm(args, rank, world, local_rank):
         peak, peak_kind = hbm_peak()
         ach = pass_a_bytes(n, nnz) / (a_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": None, "kernel": "k_pass_a (SpMV + <d,w> exact deposit)",
+                "traffic": PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz),
+                "traffic_source": "ncu dram bytes of the 128^3 launch scaled by algorithmic bytes",
+                "kernel": "k_pass_a (SpMV + <d,w> exact deposit)",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": pass_a_bytes(n, nnz), "avg_launch_ms": a_ms}
         extras["pass_ms"] = {"A": a_ms, "B": b_ms, "C": c_ms}

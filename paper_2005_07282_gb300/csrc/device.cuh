@@ -47,28 +47,41 @@ struct ExactProd {
 };
 
 __device__ __forceinline__ ExactProd exact_product(double a, double b) {
-  const uint64_t ba = (uint64_t)__double_as_longlong(a), bb = (uint64_t)__double_as_longlong(b);
-  uint32_t ea = (uint32_t)(ba >> 52) & 0x7ffu, eb = (uint32_t)(bb >> 52) & 0x7ffu;
-  uint64_t ma = ba & 0xFFFFFFFFFFFFFull, mb = bb & 0xFFFFFFFFFFFFFull;
+  // everything on 32-bit halves: exponent field, significand high part
+  // with the hidden bit (normal numbers) or without it (subnormals, whose
+  // exponent is that of field 1)
+  const uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  const uint32_t bh = (uint32_t)__double2hiint(b), bl = (uint32_t)__double2loint(b);
+  const uint32_t ea = (ah >> 20) & 0x7ffu, eb = (bh >> 20) & 0x7ffu;
   ExactProd p;
   p.bad = (ea == 0x7ffu) | (eb == 0x7ffu);
-  // normal numbers get the hidden bit; subnormals have the exponent of field 1
-  if (ea) ma |= 1ull << 52; else ea = 1;
-  if (eb) mb |= 1ull << 52; else eb = 1;
-  p.nz = (ma != 0) & (mb != 0) & !p.bad;
-  // product LSB weight 2^(ea + eb - 2150); offset from 2^kE0
-  const int o = (int)(ea + eb) - 2150 - kE0;  // 28 .. 4118
+  const uint32_t mah = (ah & 0xFFFFFu) | (ea ? 0x100000u : 0u);
+  const uint32_t mbh = (bh & 0xFFFFFu) | (eb ? 0x100000u : 0u);
+  // product LSB weight 2^(max(ea,1) + max(eb,1) - 2150); offset from 2^kE0
+  const int o = (int)(max(ea, 1u) + max(eb, 1u)) - 2150 - kE0;  // 28 .. 4118
   p.q = o >> 5;
-  const int r = o & 31;
-  const uint64_t lo = ma * mb;
-  const uint64_t hi = __umul64hi(ma, mb);  // < 2^42
-  const uint32_t v0 = (uint32_t)lo, v1 = (uint32_t)(lo >> 32), v2 = (uint32_t)hi, v3 = (uint32_t)(hi >> 32);
+  const uint32_t r = (uint32_t)o & 31u;
+  // 106-bit significand product (mah:al) x (mbh:bl) from four 32x32 products
+  const uint64_t p0 = (uint64_t)al * bl;
+  const uint64_t p1 = (uint64_t)al * mbh + (uint64_t)mah * bl;  // < 2^54
+  const uint64_t p2 = (uint64_t)mah * mbh;                      // < 2^42
+  const uint32_t v0 = (uint32_t)p0;
+  uint32_t v1, v2, v3;
+  asm("add.cc.u32 %0, %3, %4;\n\t"
+      "addc.cc.u32 %1, %5, %6;\n\t"
+      "addc.u32 %2, %7, 0;"
+      : "=r"(v1), "=r"(v2), "=r"(v3)
+      : "r"((uint32_t)(p0 >> 32)), "r"((uint32_t)p1), "r"((uint32_t)(p1 >> 32)), "r"((uint32_t)p2),
+        "r"((uint32_t)(p2 >> 32)));
   p.w0 = v0 << r;
   p.w1 = __funnelshift_l(v0, v1, r);
   p.w2 = __funnelshift_l(v1, v2, r);
   p.w3 = __funnelshift_l(v2, v3, r);
   p.w4 = __funnelshift_l(v3, 0u, r);
-  p.neg = ((ba ^ bb) >> 63) ? 0xffffffffu : 0u;
+  p.neg = (uint32_t)((int32_t)(ah ^ bh) >> 31);
+  // a zero product (either significand zero) yields five zero words: adding
+  // it anywhere changes nothing, so no separate test is needed on the fast path
+  p.nz = !p.bad;
   return p;
 }
 
@@ -97,13 +110,17 @@ __device__ __forceinline__ void smem_deposit(unsigned long long* sacc, int copy,
 // tracks the top of the magnitude range.
 struct Window {
   uint32_t W[kWin];
-  int qb;  // -1: not anchored yet
+  int qb;  // kUnanchored: not anchored yet
 };
+
+// Not anchored yet: qb far below every digit, so the first product moves
+// the window up to itself (the flush of the empty window adds nothing).
+constexpr int kUnanchored = -(1 << 20);
 
 __device__ __forceinline__ void window_init(Window& w) {
 #pragma unroll
   for (int k = 0; k < kWin; k++) w.W[k] = 0;
-  w.qb = -1;
+  w.qb = kUnanchored;
 }
 
 __device__ __forceinline__ void window_flush(Window& w, unsigned long long* sacc, int copy) {
@@ -147,18 +164,16 @@ __device__ __forceinline__ void window_add(Window& w, const ExactProd& p, bool t
 
 __device__ __forceinline__ void exact_deposit(Window& w, unsigned long long* sacc, int copy, const ExactProd& p) {
   if (!p.nz) return;
-  if (w.qb < 0) {
-    int qb = p.q - 1;
-    w.qb = qb < 0 ? 0 : (qb > kNDig - kWin ? kNDig - kWin : qb);
-  }
   const int t = p.q - w.qb;
-  if (t == 0 || t == 1) {
+  if ((unsigned)t < 2u) {
     window_add(w, p, t == 1);
-  } else if (t > 1 && p.q - 1 <= kNDig - kWin) {
-    // a larger product: move the window up to it
+  } else if (t > 1) {
+    // a larger product (or the first one): move the window up to it.  q is at
+    // most 128, so the clamped anchor keeps q - qb in {0, 1}.
     window_flush(w, sacc, copy);
-    w.qb = p.q - 1;
-    window_add(w, p, true);
+    const int qb = min(max(p.q - 1, 0), kNDig - kWin);
+    w.qb = qb;
+    window_add(w, p, p.q - qb == 1);
   } else {
     smem_deposit(sacc, copy, p);
   }

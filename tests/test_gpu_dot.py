@@ -144,3 +144,25 @@ def test_dot_exact_repeat_is_deterministic(rpcg, cuda):
     ta, tb = _dev(a, cuda), _dev(b, cuda)
     vals = {bits([rpcg.dot_exact(ta, tb).item()])[0] for _ in range(5)}
     assert len(vals) == 1
+
+
+def test_dot_exact_window_anchor_edges(rpcg, cuda, oracle_lib):
+    """The register window's first anchor: a product at the lowest digit
+    (two subnormal operands), leading zero products, and a tiny product
+    followed by ordinary ones, in every lane position of a warp."""
+    tiny = 2.0 ** -1074
+    rng = np.random.default_rng(3)
+    for n in (1, 2, 33, 4096, 100001):
+        base_a, base_b = synth.dot_family_a(n, 123)
+        for pattern in ("tiny_first", "zeros_first", "tiny_everywhere"):
+            a, b = base_a.copy(), base_b.copy()
+            if pattern == "tiny_first":
+                a[: min(n, 64)] = tiny
+                b[: min(n, 64)] = tiny * 3
+            elif pattern == "zeros_first":
+                a[: min(n, 5000)] = 0.0
+            else:
+                idx = rng.choice(n, size=max(1, n // 7), replace=False)
+                a[idx] = tiny
+                b[idx] = -tiny
+            assert same(_exact_gpu(rpcg, a, b, cuda), oracle_lib.dot_exact(a, b)), (n, pattern)
