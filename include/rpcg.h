@@ -60,6 +60,7 @@ typedef enum {
 } rpcg_variant;
 
 typedef struct rpcg_matrix_s *rpcg_matrix_t;
+typedef struct rpcg_batch_s *rpcg_batch_t;
 typedef struct rpcg_server_s *rpcg_server_t;
 
 /* Solver options.  rpcg_opts_default() fills the defaults. */
@@ -70,7 +71,7 @@ typedef struct {
     int32_t fpe_strict; /* fpe variant: 0 = recompute an inexact dot exactly (default), 1 = report RPCG_FPE_INEXACT */
     int32_t block;      /* threads per CTA of the streaming passes: 0 = auto, else 128, 256 or 512 */
     int32_t grid;       /* CTAs of the streaming passes: 0 = auto, else 1 .. 4096 */
-    int32_t reserved;
+    int32_t tile;       /* batched solves: rows per work unit, 0 = autotuned */
     double *history;    /* optional device array of max_iter + 1 doubles: relres at every loop test */
 } rpcg_opts;
 
@@ -222,6 +223,44 @@ rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double *b, double *x, int
  */
 rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double *b_host, double *x_host, int32_t v, const rpcg_opts *o,
                             rpcg_result *res, void *stream);
+
+/*
+ * Batched solves: many independent SPD systems, each with its own matrix
+ * handle, solved together (the loop of rpcg_solve for all of them at once).
+ *
+ * rpcg_batch_create -- group `count` distinct handles (the array is copied;
+ * the handles must outlive the batch and must not be used by other calls
+ * while a batch solve runs: the batch iterates in their r, d, w, inv).
+ * rpcg_batch_destroy -- release the batch (not the handles).
+ *
+ * rpcg_batch_solve -- Jacobi-PCG (the steps of rpcg_solve, Fig. 1/Fig. 2)
+ * on every system of the batch in one launch sequence: each pass is one
+ * persistent kernel over work units of at most o->tile rows of one system;
+ * each system has its own exact accumulators, scalars and convergence test
+ * and leaves the work when it stops.
+ *   b, x      host arrays of `count` device pointers (b[i], x[i]: n_i doubles;
+ *             x[i] in = x0, out = the iterate).
+ *   v         RPCG_EXBLAS (bit-identical to rpcg_solve of each system alone)
+ *             or RPCG_PLAIN.
+ *   o         options; o->history, if set, is a device array of
+ *             count x (max_iter + 1) doubles (row i for system i).
+ *             o->block (0, 128, 256) and o->tile (0 or rows per unit): a zero
+ *             picks them with the autotuner on the first solve of the batch
+ *             (short timed runs of each candidate on internal buffers; the
+ *             choice is kept for later solves).
+ *   res       host array of `count` results.
+ * Returns the worst status over the systems.  Synchronises the stream.
+ */
+rpcg_status rpcg_batch_create(rpcg_batch_t *B, int32_t count, const rpcg_matrix_t *A);
+rpcg_status rpcg_batch_destroy(rpcg_batch_t B);
+rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double *const *b, double *const *x, int32_t v, const rpcg_opts *o,
+                             rpcg_result *res, void *stream);
+/* Block size and tile the autotuner picked (0, 0 before the first autotuned solve). */
+rpcg_status rpcg_batch_tuned(rpcg_batch_t B, int32_t *block, int32_t *tile);
+
+/* One-shot form: rpcg_batch_create + rpcg_batch_solve + rpcg_batch_destroy. */
+rpcg_status rpcg_solve_batched(int32_t count, const rpcg_matrix_t *A, const double *const *b, double *const *x,
+                               int32_t v, const rpcg_opts *o, rpcg_result *res, void *stream);
 
 #ifdef __cplusplus
 }

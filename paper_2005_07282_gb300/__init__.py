@@ -27,14 +27,15 @@ VARIANTS = {"plain": PLAIN, "exblas": EXBLAS, "fpe": FPE}
 EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
-    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc",
+    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
+    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_tuned", "rpcg_solve_batched",
 ]
 
 
 class Opts(ctypes.Structure):
     _fields_ = [("tol", ctypes.c_double), ("max_iter", ctypes.c_int32), ("fpe_size", ctypes.c_int32),
                 ("fpe_strict", ctypes.c_int32), ("block", ctypes.c_int32), ("grid", ctypes.c_int32),
-                ("reserved", ctypes.c_int32), ("history", ctypes.c_void_p)]
+                ("tile", ctypes.c_int32), ("history", ctypes.c_void_p)]
 
 
 class Result(ctypes.Structure):
@@ -76,6 +77,11 @@ def lib():
         L.rpcg_dot_exact.argtypes = [i64, P, P, P, P]
         L.rpcg_dot_fpe.argtypes = [i64, P, P, i32, P, P, P]
         L.rpcg_dot_exact_noalloc.argtypes = [i64, P, P, P, P]
+        L.rpcg_batch_create.argtypes = [ctypes.POINTER(P), i32, P]
+        L.rpcg_batch_destroy.argtypes = [P]
+        L.rpcg_batch_solve.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), P, P]
+        L.rpcg_batch_tuned.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]
+        L.rpcg_solve_batched.argtypes = [i32, P, P, P, i32, ctypes.POINTER(Opts), P, P]
         L.rpcg_dot_plain.argtypes = [i64, P, P, P, P]
         L.rpcg_solve.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
         L.rpcg_solve_host.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
@@ -108,10 +114,11 @@ def _dptr(t):
     return ctypes.c_void_p(t.data_ptr())
 
 
-def make_opts(tol=1e-8, max_iter=1000, fpe_size=8, fpe_strict=0, block=0, grid=0, history=None) -> Opts:
+def make_opts(tol=1e-8, max_iter=1000, fpe_size=8, fpe_strict=0, block=0, grid=0, tile=0, history=None) -> Opts:
     o = Opts()
     lib().rpcg_opts_default(ctypes.byref(o))
     o.tol, o.max_iter, o.fpe_size, o.fpe_strict, o.block, o.grid = tol, max_iter, fpe_size, fpe_strict, block, grid
+    o.tile = tile
     o.history = None if history is None else _dptr(history).value
     return o
 
@@ -235,3 +242,43 @@ class Matrix:
         if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
             _check(st, "rpcg_solve_host")
         return r.as_dict()
+
+
+class Batch:
+    """A batch of matrix handles solved together (rpcg_batch_*)."""
+
+    def __init__(self, mats):
+        self.mats = list(mats)
+        arr = (ctypes.c_void_p * len(self.mats))(*[m._h.value for m in self.mats])
+        self._h = ctypes.c_void_p()
+        _check(lib().rpcg_batch_create(ctypes.byref(self._h), len(self.mats), arr), "rpcg_batch_create")
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().rpcg_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def solve(self, bs, xs, variant="exblas", stream=None, **opts):
+        """Solve every system: bs, xs lists of device tensors (xs updated in place)."""
+        n = len(self.mats)
+        assert len(bs) == n and len(xs) == n
+        barr = (ctypes.c_void_p * n)(*[_dptr(t).value for t in bs])
+        xarr = (ctypes.c_void_p * n)(*[_dptr(t).value for t in xs])
+        res = (Result * n)()
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o = make_opts(**opts)
+        st = lib().rpcg_batch_solve(self._h, barr, xarr, v, ctypes.byref(o), res, _stream(stream))
+        if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
+            _check(st, "rpcg_batch_solve")
+        return [r.as_dict() for r in res]
+
+    def tuned(self):
+        b, t = ctypes.c_int32(), ctypes.c_int32()
+        lib().rpcg_batch_tuned(self._h, ctypes.byref(b), ctypes.byref(t))
+        return b.value, t.value

@@ -189,6 +189,9 @@ __device__ __forceinline__ void smem_to_global(const unsigned long long* sacc, u
     for (int c = 0; c < kCopies; c++) s += sacc[k * kCopies + c];
     if (s) atomicAdd(gacc + k, s);
   }
+  // make this thread's additions visible device-wide before the CTA announces
+  // its arrival (the last CTA reads the digits right after)
+  __threadfence();
 }
 
 // Zero `nacc` shared-memory accumulators (kNDig * kCopies words each).
@@ -311,6 +314,25 @@ __device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&er
 }
 
 // ------------------------------------------------------------------ misc
+
+// Fixed-shape sum over a CTA (warp shuffles, then warp 0 over the warp
+// sums); the result is valid in thread 0.  sw: 32 doubles of shared memory.
+template <int BLOCK>
+__device__ __forceinline__ double block_sum_fixed(double v, double* sw) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sw[warp] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (warp == 0) {
+    s = lane < BLOCK / 32 ? sw[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
+  }
+  return s;
+}
 
 __device__ __forceinline__ bool is_last_block(unsigned int* counter) {
   __shared__ bool last;

@@ -184,24 +184,6 @@ __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __re
 
 // ------------------------------------------------------------------ plain dot
 template <int BLOCK>
-__device__ __forceinline__ double block_sum_fixed(double v, double* sw) {
-  // fixed-shape tree: warp shuffles, then warp 0 over the warp sums
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = __dadd_rn(v, __shfl_down_sync(0xffffffffu, v, o));
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) sw[warp] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (warp == 0) {
-    s = lane < BLOCK / 32 ? sw[lane] : 0.0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s = __dadd_rn(s, __shfl_down_sync(0xffffffffu, s, o));
-  }
-  return s;  // valid in thread 0
-}
-
-template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_dot_plain(int64_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, DotScratch* ws, double* out) {
   __shared__ double sw[32];

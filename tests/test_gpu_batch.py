@@ -1,0 +1,119 @@
+"""Batched solves: each system's result equals solving it alone, bit for
+bit (exblas), for any tile size and with the autotuner; per-system
+statuses are independent."""
+import numpy as np
+import pytest
+import scipy.sparse
+
+import synth
+from conftest import bits
+
+pytestmark = pytest.mark.gpu
+
+SEED = synth.BASE_SEED + 4
+
+
+def _dev(x, cuda):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64)).to(cuda)
+
+
+def _csr_dense(M):
+    S = scipy.sparse.csr_matrix(M)
+    S.sort_indices()
+    return synth.CSR(M.shape[0], S.indptr.astype(np.int32), S.indices.astype(np.int32), S.data.astype(np.float64))
+
+
+def _systems():
+    mats, rhs = [], []
+    for k, s in enumerate([9, 3, 14, 1, 6, 11, 2, 8]):
+        A, _ = synth.diffusion7(s, SEED + k)
+        mats.append(A)
+        rhs.append(synth.rhs_uniform(A.n, SEED + 100 + k))
+    return mats, rhs
+
+
+def _solo(rpcg, M, b, cuda, **kw):
+    import torch
+    x = torch.zeros(M.n, dtype=torch.float64, device=cuda)
+    r = M.solve(b, x, **kw)
+    return r, x.cpu().numpy()
+
+
+@pytest.mark.parametrize("tile", [32, 100, 4096, 0])
+def test_batch_bit_identical_to_solo(rpcg, cuda, tile):
+    import torch
+    mats, rhs = _systems()
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    bs = [_dev(b, cuda) for b in rhs]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    B = rpcg.Batch(Ms)
+    res = B.solve(bs, xs, variant="exblas", tol=1e-10, max_iter=3000, tile=tile, block=128 if tile == 100 else 0)
+    for i, (M, b) in enumerate(zip(Ms, bs)):
+        r, x = _solo(rpcg, M, b, cuda, variant="exblas", tol=1e-10, max_iter=3000)
+        assert res[i]["iterations"] == r["iterations"], i
+        assert res[i]["status"] == r["status"] == 0, i
+        assert bits([res[i]["relres"]])[0] == bits([r["relres"]])[0]
+        assert np.array_equal(bits(xs[i].cpu().numpy()), bits(x)), i
+    if tile == 0:
+        blk, tl = B.tuned()
+        assert blk in (128, 256) and tl in (2048, 8192, 32768)
+    B.close()
+
+
+def test_batch_matches_oracle_and_history(rpcg, cuda, oracle_lib):
+    import torch
+    mats, rhs = _systems()
+    mats, rhs = mats[:3], rhs[:3]
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    hist = torch.full((3, 3001), float("nan"), dtype=torch.float64, device=cuda)
+    B = rpcg.Batch(Ms)
+    res = B.solve([_dev(b, cuda) for b in rhs], xs, tol=1e-10, max_iter=3000, tile=64, history=hist)
+    for i, (A, b) in enumerate(zip(mats, rhs)):
+        ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, tol=1e-10, max_iter=3000)
+        assert res[i]["iterations"] == ref["iterations"]
+        assert np.array_equal(bits(xs[i].cpu().numpy()), bits(ref["x"]))
+        h = hist[i, : ref["iterations"] + 1].cpu().numpy()
+        assert np.array_equal(bits(h), bits(ref["history"]))
+
+
+def test_batch_mixed_statuses(rpcg, cuda, oracle_lib):
+    import torch
+    A0, _ = synth.diffusion7(5, SEED)
+    mats = [A0, _csr_dense(np.array([[1.0, 2.0], [2.0, 1.0]])), _csr_dense(np.array([[4.0]])), A0]
+    # the last system repeats A0's pattern but is a distinct handle with b = 0
+    rhs = [synth.rhs_uniform(A0.n, 1), np.array([1.0, -1.0]), np.array([3.0]), np.zeros(A0.n)]
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    xs = [torch.ones(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    res = rpcg.Batch(Ms).solve([_dev(b, cuda) for b in rhs], xs, tol=1e-10, max_iter=50, tile=16)
+    for i in range(4):
+        x0 = np.ones(mats[i].n)
+        ref = oracle_lib.pcg(mats[i], rhs[i], x0=x0, variant=oracle_lib.EXACT, tol=1e-10, max_iter=50)
+        assert res[i]["status"] == ref["status"], (i, res[i], ref["status"])
+        assert res[i]["iterations"] == ref["iterations"], i
+        if ref["status"] >= 0:
+            assert np.array_equal(bits(xs[i].cpu().numpy()), bits(ref["x"])), i
+    assert res[1]["status"] == rpcg.ERR_NOT_SPD
+    assert res[3]["iterations"] == 0 and not xs[3].any().item()
+
+
+def test_batch_plain_converges(rpcg, cuda):
+    import torch
+    mats, rhs = _systems()
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    res = rpcg.Batch(Ms).solve([_dev(b, cuda) for b in rhs], xs, variant="plain", tol=1e-10, max_iter=3000)
+    assert all(r["status"] == 0 and r["relres"] < 1e-10 for r in res)
+
+
+def test_batch_rejects_duplicates_and_fpe(rpcg, cuda):
+    import torch
+    A, _ = synth.diffusion7(4, 1)
+    M = rpcg.Matrix.from_csr(A)
+    with pytest.raises(rpcg.RpcgError):
+        rpcg.Batch([M, M])
+    B = rpcg.Batch([M])
+    x = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    with pytest.raises(rpcg.RpcgError):
+        B.solve([_dev(synth.rhs_uniform(A.n, 2), cuda)], [x], variant="fpe")
