@@ -51,6 +51,8 @@ def parse():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain/fpe/dot/e2e side measurements")
+    ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
+                    help="only the batched workload: COUNT variable-diffusion systems, s ~ U{8..64}, tol 1e-10")
     ap.add_argument("--dot-only", type=int, default=0, metavar="LOG2N",
                     help="only time the exact, fpe and plain dots on 2^LOG2N U[-1,1] pairs")
     ap.add_argument("--eager", action="store_true",
@@ -404,8 +406,83 @@ def dot_arm(args):
                       "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
 
 
+def batch_systems(count, seed):
+    """The batched workload: variable-coefficient 7-point diffusion systems on
+    s^3 grids, s uniform in [8, 64], b ~ U[-1, 1] per system."""
+    sides = synth.uniform_int(synth.stream_seed(seed, 50), count, 8, 64)
+    mats, rhs = [], []
+    for i, s in enumerate(sides.tolist()):
+        A, _ = synth.diffusion7(int(s), synth.stream_seed(seed, 1000 + i))
+        mats.append(A)
+        rhs.append(synth.rhs_uniform(A.n, synth.stream_seed(seed, 5000 + i)))
+    return mats, rhs
+
+
+def batch_arm(args):
+    """--batch COUNT: one batched solve of COUNT systems per step (exblas,
+    tol 1e-10), against solving the same systems one after the other."""
+    import torch
+
+    import paper_2005_07282_gb300 as P
+    from paper_2005_07282_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    t0 = time.perf_counter()
+    mats, rhs = batch_systems(args.batch, synth.BASE_SEED + 3)
+    gen_s = time.perf_counter() - t0
+    Ms = [P.Matrix.from_csr(A) for A in mats]
+    bs = [torch.from_numpy(b).to(dev) for b in rhs]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device=dev) for A in mats]
+    opts = dict(tol=1e-10, max_iter=args.max_iter)
+    Bt = P.Batch(Ms)
+
+    def run():
+        for x in xs:
+            x.zero_()
+        return Bt.solve(bs, xs, variant="exblas", **opts)
+
+    for _ in range(args.warmup):
+        res = run()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        res = run()
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    its = [r["iterations"] for r in res]
+    batch_x = [x.cpu().numpy().copy() for x in xs]
+    # the same systems solved one by one (graph per system), and the bit check
+    for x in xs:
+        x.zero_()
+    torch.cuda.synchronize()
+    e0.record()
+    solo = [M.solve(b, x, variant="exblas", **opts) for M, b, x in zip(Ms, bs, xs)]
+    e1.record()
+    torch.cuda.synchronize()
+    solo_ms = e0.elapsed_time(e1)
+    same = all(np.array_equal(a.view(np.int64), x.cpu().numpy().view(np.int64)) for a, x in zip(batch_x, xs)) and \
+        all(r["iterations"] == s["iterations"] for r, s in zip(res, solo))
+    rows = sum(A.n for A in mats)
+    nnz = sum(A.nnz for A in mats)
+    blk, tile = Bt.tuned()
+    print(json.dumps({"workload": f"batch of {args.batch} diffusion7 systems, s~U{{8..64}}, tol 1e-10, exblas",
+                      "rows": rows, "nnz": nnz, "solves_per_s": args.batch / (ms / 1e3), "ms_per_batch": ms,
+                      "iterations": {"total": sum(its), "min": min(its), "max": max(its),
+                                     "mean": sum(its) / len(its)},
+                      "system_iters_per_s": sum(its) / (ms / 1e3),
+                      "sequential_solo_ms": solo_ms, "speedup_vs_sequential": solo_ms / ms,
+                      "bit_identical_to_solo": bool(same), "statuses": sorted(set(r["status"] for r in res)),
+                      "autotuned": {"block": blk, "tile": tile}, "steps": args.steps, "warmup": args.warmup,
+                      "generation_s": gen_s}), flush=True)
+
+
 def main():
     args = parse()
+    if args.batch:
+        batch_arm(args)
+        return
     if args.dot_only:
         dot_arm(args)
         return
