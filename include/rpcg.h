@@ -262,6 +262,58 @@ rpcg_status rpcg_batch_tuned(rpcg_batch_t B, int32_t *block, int32_t *tile);
 rpcg_status rpcg_solve_batched(int32_t count, const rpcg_matrix_t *A, const double *const *b, double *const *x,
                                int32_t v, const rpcg_opts *o, rpcg_result *res, void *stream);
 
+/*
+ * Serving: a request loop that batches solves of different sizes as they
+ * arrive (continuous batching).  A scheduler thread admits queued requests
+ * into a table of `max_slots` slots while the device bytes in use (cached
+ * matrices plus the vectors of running systems) stay within the HBM budget;
+ * matrices stay on the device in an LRU cache keyed by the host arrays that
+ * named them, so repeated requests on the same matrix do not upload it
+ * again.  Running systems advance together, 16 iterations per scheduling
+ * step, through the batched passes of rpcg_batch_solve; systems that stop
+ * leave and queued ones join between steps.  Every result is bit-identical
+ * to rpcg_solve of the same system alone (exact dots).  The paper has no
+ * serving layer; this is the deployment form of its solver (Sec. 4).
+ *
+ * rpcg_server_create -- start the loop on the current device.
+ *   hbm_budget_bytes  >= 1 MiB; requests that can never fit fail with
+ *                     RPCG_ERR_OOM.
+ * rpcg_server_submit -- queue one solve (the exblas variant; tol and
+ *   max_iter from o).  rowptr/col/val (n, nnz) and b, and x0 if not NULL
+ *   (else x0 = 0), are host arrays that must stay valid and unchanged until
+ *   rpcg_server_wait returns for this ticket.  Never blocks on the GPU.
+ * rpcg_server_wait -- wait up to timeout_us (< 0: forever) for a ticket;
+ *   copies x into x_host (n doubles, may be NULL), fills res and, if not
+ *   NULL, the time the request queued and the time it was served.  Returns
+ *   res->status, or RPCG_ERR_TIMEOUT (the ticket stays valid) or
+ *   RPCG_ERR_INVALID (unknown or already collected ticket).
+ * rpcg_server_stats -- counters.
+ * rpcg_server_destroy -- finish every queued request, stop the loop, free
+ *   all device memory.  Results not collected are dropped.
+ */
+typedef struct {
+    double queue_us;   /* submit -> admitted into a slot */
+    double service_us; /* admitted -> result back in host memory */
+} rpcg_server_timing;
+
+typedef struct {
+    uint64_t completed;       /* requests finished (including failures) */
+    uint64_t failed;          /* requests finished with a negative status */
+    uint64_t queued;          /* requests waiting for a slot */
+    uint64_t chunks;          /* scheduling steps run */
+    uint64_t bytes_in_use;    /* device bytes held by cached matrices and running systems */
+    uint64_t matrices_cached; /* matrices resident on the device */
+} rpcg_server_stats_t;
+
+rpcg_status rpcg_server_create(rpcg_server_t *srv, size_t hbm_budget_bytes, int32_t max_slots);
+rpcg_status rpcg_server_submit(rpcg_server_t srv, int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
+                               const double *val, const double *b, const double *x0, int32_t v, const rpcg_opts *o,
+                               uint64_t *ticket);
+rpcg_status rpcg_server_wait(rpcg_server_t srv, uint64_t ticket, double *x_host, rpcg_result *res,
+                             rpcg_server_timing *timing, int64_t timeout_us);
+rpcg_status rpcg_server_stats(rpcg_server_t srv, rpcg_server_stats_t *st);
+rpcg_status rpcg_server_destroy(rpcg_server_t srv);
+
 #ifdef __cplusplus
 }
 #endif

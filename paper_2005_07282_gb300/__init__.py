@@ -28,7 +28,8 @@ EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
     "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
-    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_tuned", "rpcg_solve_batched",
+    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
+    "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy",
 ]
 
 
@@ -45,6 +46,15 @@ class Result(ctypes.Structure):
     def as_dict(self):
         return dict(iterations=self.iterations, status=self.status, relres=self.relres, tau=self.tau,
                     fpe_inexact_count=self.fpe_inexact_count)
+
+
+class ServerTiming(ctypes.Structure):
+    _fields_ = [("queue_us", ctypes.c_double), ("service_us", ctypes.c_double)]
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64), ("queued", ctypes.c_uint64),
+                ("chunks", ctypes.c_uint64), ("bytes_in_use", ctypes.c_uint64), ("matrices_cached", ctypes.c_uint64)]
 
 
 class RpcgError(RuntimeError):
@@ -82,6 +92,13 @@ def lib():
         L.rpcg_batch_solve.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), P, P]
         L.rpcg_batch_tuned.argtypes = [P, ctypes.POINTER(i32), ctypes.POINTER(i32)]
         L.rpcg_solve_batched.argtypes = [i32, P, P, P, i32, ctypes.POINTER(Opts), P, P]
+        L.rpcg_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, i32]
+        L.rpcg_server_submit.argtypes = [P, i32, i32, P, P, P, P, P, i32, ctypes.POINTER(Opts),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+        L.rpcg_server_wait.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(Result), ctypes.POINTER(ServerTiming),
+                                       ctypes.c_int64]
+        L.rpcg_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
+        L.rpcg_server_destroy.argtypes = [P]
         L.rpcg_dot_plain.argtypes = [i64, P, P, P, P]
         L.rpcg_solve.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
         L.rpcg_solve_host.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), ctypes.POINTER(Result), P]
@@ -282,3 +299,62 @@ class Batch:
         b, t = ctypes.c_int32(), ctypes.c_int32()
         lib().rpcg_batch_tuned(self._h, ctypes.byref(b), ctypes.byref(t))
         return b.value, t.value
+
+
+class Server:
+    """The serving loop (rpcg_server_*).  Host arrays passed to submit() are
+    kept referenced until their ticket has been waited for."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 256):
+        self._h = ctypes.c_void_p()
+        _check(lib().rpcg_server_create(ctypes.byref(self._h), int(hbm_budget_bytes), int(max_slots)),
+               "rpcg_server_create")
+        self._keep = {}
+
+    def submit(self, A, b: np.ndarray, x0=None, tol=1e-8, max_iter=1000) -> int:
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        cl = np.ascontiguousarray(A.col, dtype=np.int32)
+        vl = np.ascontiguousarray(A.val, dtype=np.float64)
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        o = make_opts(tol=tol, max_iter=max_iter)
+        t = ctypes.c_uint64()
+        _check(lib().rpcg_server_submit(self._h, A.n, int(vl.size), rp.ctypes.data, cl.ctypes.data, vl.ctypes.data,
+                                        b.ctypes.data, None if x0 is None else x0.ctypes.data, EXBLAS,
+                                        ctypes.byref(o), ctypes.byref(t)), "rpcg_server_submit")
+        self._keep[t.value] = (rp, cl, vl, b, x0, A.n)
+        return t.value
+
+    def wait(self, ticket: int, timeout_us: int = -1):
+        """Returns (x, result dict with queue_us/service_us)."""
+        n = self._keep[ticket][5] if ticket in self._keep else 0
+        x = np.empty(n, dtype=np.float64)
+        r = Result()
+        tm = ServerTiming()
+        st = lib().rpcg_server_wait(self._h, ticket, x.ctypes.data if n else None, ctypes.byref(r),
+                                    ctypes.byref(tm), timeout_us)
+        if st == ERR_TIMEOUT:
+            raise TimeoutError(f"ticket {ticket} not done within {timeout_us} us")
+        if st in (ERR_INVALID, ERR_CUDA):
+            _check(st, "rpcg_server_wait")
+        self._keep.pop(ticket, None)
+        d = r.as_dict()
+        d["queue_us"], d["service_us"] = tm.queue_us, tm.service_us
+        return x, d
+
+    def stats(self) -> dict:
+        s = ServerStats()
+        lib().rpcg_server_stats(self._h, ctypes.byref(s))
+        return {k: getattr(s, k) for k, _ in ServerStats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().rpcg_server_destroy(self._h)
+            self._h = ctypes.c_void_p()
+        self._keep = {}
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -25,369 +25,8 @@
 #include <tuple>
 #include <vector>
 
-#include "device.cuh"
+#include "batch.cuh"
 #include "host.h"
-#include "solver.cuh"
-
-namespace rpcg {
-
-struct SysDev {
-  MatDev m;
-  const double* b;
-  double* x;
-  double *r, *d, *w, *inv;
-};
-
-struct SysState {
-  double rho, beta, beta_old, tau, gamma, bnorm, rel;
-  int iter, status, bad_row, bzero, active, pad;
-};
-
-struct Unit {
-  int sys, r0, r1;
-};
-
-struct BatchArgs {
-  double* history;  // count x (max_iter + 1), or null
-  double tol;
-  int max_iter;
-  int count;
-};
-
-struct BatchScratchHead {
-  int active_count;
-  int pad;
-};
-
-// per-system reduction scratch (digits, arrival counter, flags)
-struct SysRed {
-  unsigned long long digits[3][kNDig];
-  unsigned int counter;
-  unsigned int flags;
-};
-
-__device__ __forceinline__ void b_stop(SysState* st, BatchScratchHead* head) {
-  if (st->active) {
-    st->active = 0;
-    atomicSub(&head->active_count, 1);
-  }
-}
-
-// ------------------------------------------------------------------ unit driver
-
-struct UnitSmem {
-  double sw[32];
-  long long dig[kNDig];
-  uint32_t D[kNDig];
-  double value[3];
-  bool last;
-};
-
-// Process every unit of the active systems.  row_fn(sys, row, R, sacc)
-// deposits into the reducer; fin_fn(sys, values) runs in thread 0 of the
-// CTA that completes a system.  `need_active` = 0 processes every system
-// (the set-up pass).
-template <int V, int NACC, int BLOCK, class RowFn, class FinFn>
-__device__ __forceinline__ void for_units(const Unit* __restrict__ units, int nunits, const int* __restrict__ unit_count,
-                                          SysState* states, SysRed* red, double* unit_partials, bool need_active,
-                                          unsigned char* smem, RowFn row_fn, FinFn fin_fn) {
-  unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem);
-  UnitSmem* us = reinterpret_cast<UnitSmem*>(smem + (V == RPCG_EXBLAS ? NACC * kNDig * kCopies * 8 : 0));
-  const int copy = threadIdx.x & (kCopies - 1);
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const Unit U = units[u];
-    if (need_active && !states[U.sys].active) continue;  // uniform over the CTA
-    Window win[NACC];
-    double acc[NACC];
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < NACC; j++) {
-      window_init(win[j]);
-      acc[j] = 0.0;
-    }
-    if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc, NACC);
-    __syncthreads();
-    for (int row = U.r0 + threadIdx.x; row < U.r1; row += BLOCK) {
-      row_fn(U.sys, row, [&](int j, double a, double b) {
-        if constexpr (V == RPCG_EXBLAS) {
-          const ExactProd e = exact_product(a, b);
-          bad |= e.bad;
-          exact_deposit(win[j], sacc + j * kNDig * kCopies, copy, e);
-        } else {
-          acc[j] = __fma_rn(a, b, acc[j]);
-        }
-      });
-    }
-    SysRed* R = red + U.sys;
-    if constexpr (V == RPCG_EXBLAS) {
-#pragma unroll
-      for (int j = 0; j < NACC; j++) window_flush(win[j], sacc + j * kNDig * kCopies, copy);
-      if (bad) atomicOr(&R->flags, 1u);
-      __syncthreads();
-      for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, R->digits[j]);
-    } else {
-      for (int j = 0; j < NACC; j++) {
-        const double sblk = block_sum_fixed<BLOCK>(acc[j], us->sw);
-        if (threadIdx.x == 0) unit_partials[(size_t)u * 3 + j] = sblk;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned int prev = atomicAdd(&R->counter, 1u);
-      us->last = (prev == (unsigned)unit_count[U.sys] - 1u);
-    }
-    __syncthreads();
-    if (us->last) {
-      __threadfence();
-      if constexpr (V == RPCG_EXBLAS) {
-        for (int j = 0; j < NACC; j++) {
-          for (int k = threadIdx.x; k < kNDig; k += BLOCK) us->dig[k] = (long long)atomicExch(&R->digits[j][k], 0ull);
-          __syncthreads();
-          if (threadIdx.x == 0) us->value[j] = round_digits(us->dig, us->D);
-          __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-          const unsigned int f = atomicExch(&R->flags, 0u);
-          if (f & 1u)
-            for (int j = 0; j < NACC; j++) us->value[j] = __longlong_as_double(0x7FF8000000000000ll);
-        }
-      } else {
-        if (threadIdx.x == 0) {
-          // the system's units are contiguous: sum their partials in unit order
-          int first = u;
-          while (first > 0 && units[first - 1].sys == U.sys) first--;
-          for (int j = 0; j < NACC; j++) {
-            double v = 0.0;
-            for (int k = 0; k < unit_count[U.sys]; k++) v = __dadd_rn(v, __ldcg(&unit_partials[(size_t)(first + k) * 3 + j]));
-            us->value[j] = v;
-          }
-        }
-      }
-      if (threadIdx.x == 0) {
-        R->counter = 0;
-        fin_fn(U.sys, us->value);
-      }
-    }
-    __syncthreads();
-  }
-}
-
-template <int V>
-__host__ __device__ constexpr size_t b_smem(int nacc) {
-  return (V == RPCG_EXBLAS ? (size_t)nacc * kNDig * kCopies * 8 : 0) + sizeof(UnitSmem) + 16;
-}
-
-// ------------------------------------------------------------------ kernels
-
-__global__ void k_b_init(const SysDev* __restrict__ sys, SysState* st, BatchScratchHead* head, int count,
-                         int nactive) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
-    SysState& t = st[s];
-    t.rho = t.beta = t.beta_old = t.gamma = t.bnorm = 0.0;
-    t.tau = t.rel = __longlong_as_double(0x7FF8000000000000ll);
-    t.iter = 0;
-    t.status = 0;
-    t.bad_row = INT_MAX;
-    t.bzero = 0;
-    t.active = sys[s].m.n > 0 ? 1 : 0;  // an empty system has no units: done at once
-    t.pad = 0;
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) head->active_count = nactive;
-}
-
-// inverse diagonal and A x0 for every unit
-__global__ void k_b_inv_q(const SysDev* __restrict__ sys, const Unit* __restrict__ units, int nunits, SysState* st) {
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const Unit U = units[u];
-    const SysDev& S = sys[U.sys];
-    for (int i = U.r0 + threadIdx.x; i < U.r1; i += blockDim.x) {
-      double aii = 0.0;
-      bool found = false;
-      const int len = S.m.rowptr[i + 1] - S.m.rowptr[i];
-      const long long base = sell_index(S.m, i, 0);
-      for (int k = 0; k < len; k++) {
-        if (S.m.col[base + 32ll * k] == i) {
-          aii = S.m.val[base + 32ll * k];
-          found = true;
-        }
-      }
-      if (!found || !(aii > 0.0)) {
-        atomicMin(&st[U.sys].bad_row, i);
-        S.inv[i] = 0.0;
-      } else {
-        S.inv[i] = __drcp_rn(aii);
-      }
-      S.w[i] = sell_row(S.m, i, S.x);
-    }
-  }
-}
-
-template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_setup(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                   int nunits, const int* __restrict__ unit_count, SysState* st,
-                                                   SysRed* red, double* unit_partials, BatchScratchHead* head,
-                                                   const BatchArgs* args) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  for_units<V, 3, BLOCK>(
-      units, nunits, unit_count, st, red, unit_partials, false, smem,
-      [&](int s, int i, auto dep) {
-        const SysDev& S = sys[s];
-        const double bi = S.b[i];
-        const double ri = __dsub_rn(bi, S.w[i]);
-        const double zi = __dmul_rn(S.inv[i], ri);
-        S.r[i] = ri;
-        S.d[i] = zi;
-        dep(0, zi, ri);
-        dep(1, ri, ri);
-        dep(2, bi, bi);
-      },
-      [&](int s, const double* v) {
-        SysState* t = st + s;
-        const SysDev& S = sys[s];
-        if (t->bad_row < S.m.n) {
-          const int i = t->bad_row;
-          double aii = 0.0;
-          const int len = S.m.rowptr[i + 1] - S.m.rowptr[i];
-          const long long base = sell_index(S.m, i, 0);
-          for (int k = 0; k < len; k++)
-            if (S.m.col[base + 32ll * k] == i) aii = S.m.val[base + 32ll * k];
-          t->status = isfinite(aii) ? RPCG_ERR_NOT_SPD : RPCG_ERR_NONFINITE;
-          b_stop(t, head);
-          return;
-        }
-        if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
-          t->status = RPCG_ERR_NONFINITE;
-          b_stop(t, head);
-          return;
-        }
-        t->beta = v[0];
-        const double bnorm = __dsqrt_rn(v[2]);
-        t->bnorm = bnorm;
-        double* hist = args->history ? args->history + (size_t)s * (args->max_iter + 1) : nullptr;
-        if (bnorm == 0.0) {
-          t->bzero = 1;
-          t->rel = 0.0;
-          t->tau = 0.0;
-          if (hist) hist[0] = 0.0;
-          b_stop(t, head);
-          return;
-        }
-        t->tau = v[1];
-        t->rel = __ddiv_rn(__dsqrt_rn(v[1]), bnorm);
-        if (hist) hist[0] = t->rel;
-        if (!((t->rel >= args->tol) && (0 < args->max_iter))) b_stop(t, head);
-      });
-}
-
-template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_pass_a(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                    int nunits, const int* __restrict__ unit_count, SysState* st,
-                                                    SysRed* red, double* unit_partials, BatchScratchHead* head) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  for_units<V, 1, BLOCK>(
-      units, nunits, unit_count, st, red, unit_partials, true, smem,
-      [&](int s, int i, auto dep) {
-        const SysDev& S = sys[s];
-        const double v = sell_row(S.m, i, S.d);
-        S.w[i] = v;
-        dep(0, __ldg(S.d + i), v);
-      },
-      [&](int s, const double* v) {
-        SysState* t = st + s;
-        const double dw = v[0];
-        if (!isfinite(dw)) {
-          t->status = RPCG_ERR_NONFINITE;
-          b_stop(t, head);
-          return;
-        }
-        if (!(dw > 0.0)) {
-          t->status = RPCG_ERR_NOT_SPD;
-          b_stop(t, head);
-          return;
-        }
-        t->beta_old = t->beta;
-        t->rho = __ddiv_rn(t->beta, dw);
-      });
-}
-
-template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_pass_b(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                    int nunits, const int* __restrict__ unit_count, SysState* st,
-                                                    SysRed* red, double* unit_partials, BatchScratchHead* head,
-                                                    const BatchArgs* args) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  for_units<V, 2, BLOCK>(
-      units, nunits, unit_count, st, red, unit_partials, true, smem,
-      [&](int s, int i, auto dep) {
-        const SysDev& S = sys[s];
-        const double rho = st[s].rho;
-        const double di = S.d[i], wi = S.w[i];
-        const double xi = __fma_rn(rho, di, S.x[i]);
-        const double ri = __fma_rn(-rho, wi, S.r[i]);
-        const double zi = __dmul_rn(S.inv[i], ri);
-        S.x[i] = xi;
-        S.r[i] = ri;
-        dep(0, zi, ri);
-        dep(1, ri, ri);
-      },
-      [&](int s, const double* v) {
-        SysState* t = st + s;
-        const double beta = v[0], tau = v[1];
-        t->beta = beta;
-        t->tau = tau;
-        if (!isfinite(beta) || !isfinite(tau)) {
-          t->status = RPCG_ERR_NONFINITE;
-          t->iter += 1;
-          b_stop(t, head);
-          return;
-        }
-        t->gamma = __ddiv_rn(beta, t->beta_old);
-        t->iter += 1;
-        t->rel = __ddiv_rn(__dsqrt_rn(tau), t->bnorm);
-        if (args->history) args->history[(size_t)s * (args->max_iter + 1) + t->iter] = t->rel;
-        if (tau > 0.0 && !(beta > 0.0)) {
-          t->status = RPCG_ERR_NOT_SPD;
-          b_stop(t, head);
-          return;
-        }
-        if (!((t->rel >= args->tol) && (t->iter < args->max_iter))) {
-          t->active = 2;  // finished this iteration: pass C still updates d (unobservable), then it stops
-        }
-      });
-}
-
-// S7 for every system that ran pass B this iteration; systems that finished
-// in pass B leave the active set here.
-template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_pass_c(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                    int nunits, SysState* st) {
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const Unit U = units[u];
-    const SysState& t = st[U.sys];
-    if (!t.active || t.status != 0) continue;
-    const SysDev& S = sys[U.sys];
-    const double g = t.gamma;
-    for (int i = U.r0 + threadIdx.x; i < U.r1; i += BLOCK) {
-      const double zi = __dmul_rn(S.inv[i], S.r[i]);
-      S.d[i] = __fma_rn(g, S.d[i], zi);
-    }
-  }
-}
-
-// Retire the systems that finished in pass B and set the loop condition.
-__global__ void k_b_cond(SysState* st, int count, BatchScratchHead* head, cudaGraphConditionalHandle cond) {
-  for (int s = threadIdx.x; s < count; s += blockDim.x) {
-    if (st[s].active == 2) b_stop(st + s, head);
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    cudaGraphSetConditional(cond, atomicAdd(&head->active_count, 0) > 0 ? 1u : 0u);
-  }
-}
-
-}  // namespace rpcg
 
 struct rpcg_batch_s {
   int count = 0;
@@ -399,13 +38,12 @@ struct rpcg_batch_s {
   rpcg::SysState* h_state = nullptr;  // pinned
   rpcg::SysRed* d_red = nullptr;
   rpcg::BatchScratchHead* d_head = nullptr;
-  rpcg::BatchArgs* d_args = nullptr;
-  rpcg::BatchArgs* h_args = nullptr;  // pinned
   // per tile size: units, unit counts, partials
   struct Layout {
     rpcg::Unit* units = nullptr;
     int* unit_count = nullptr;
     double* partials = nullptr;
+    int* d_nunits = nullptr;  // the unit count, read by the kernels
     int nunits = 0;
   };
   std::map<int, Layout> layouts;
@@ -437,6 +75,8 @@ static rpcg_status batch_layout(rpcg_batch_t B, int tile, rpcg_batch_s::Layout**
   RPCG_CUDA_TRY(cudaMalloc(&L.units, std::max<size_t>(1, units.size()) * sizeof(Unit)));
   RPCG_CUDA_TRY(cudaMalloc(&L.unit_count, std::max<size_t>(1, counts.size()) * sizeof(int)));
   RPCG_CUDA_TRY(cudaMalloc(&L.partials, std::max<size_t>(1, units.size()) * 3 * sizeof(double)));
+  RPCG_CUDA_TRY(cudaMalloc(&L.d_nunits, sizeof(int)));
+  RPCG_CUDA_TRY(cudaMemcpy(L.d_nunits, &L.nunits, sizeof(int), cudaMemcpyHostToDevice));
   if (!units.empty()) RPCG_CUDA_TRY(cudaMemcpy(L.units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice));
   RPCG_CUDA_TRY(cudaMemcpy(L.unit_count, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice));
   B->layouts[tile] = L;
@@ -485,9 +125,8 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
   SysState* sst = B->d_state;
   SysRed* red = B->d_red;
   BatchScratchHead* head = B->d_head;
-  BatchArgs* args = B->d_args;
   Unit* units = L->units;
-  int nunits = L->nunits;
+  int* nunits = L->d_nunits;
   int* ucount = L->unit_count;
   double* partials = L->partials;
   int count = B->count;
@@ -502,7 +141,7 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
     RPCG_CUDA_TRY(add_node(g, &n_q, &n_init, 1, (const void*)k_b_inv_q, g_q, BLOCK, 0, a));
   }
   {
-    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head, &args};
+    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head};
     RPCG_CUDA_TRY(add_node(g, &n_setup, &n_q, 1, (const void*)k_b_setup<V, BLOCK>, g_setup, BLOCK, sm3, a));
   }
   {
@@ -522,7 +161,7 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
     RPCG_CUDA_TRY(add_node(body, &b_a, nullptr, 0, (const void*)k_b_pass_a<V, BLOCK>, g_a, BLOCK, sm1, a));
   }
   {
-    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head, &args};
+    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head};
     RPCG_CUDA_TRY(add_node(body, &b_b, &b_a, 1, (const void*)k_b_pass_b<V, BLOCK>, g_b, BLOCK, sm2, a));
   }
   {
@@ -570,15 +209,14 @@ static void batch_free(rpcg_batch_t B) {
     cudaFree(kv.second.units);
     cudaFree(kv.second.unit_count);
     cudaFree(kv.second.partials);
+    cudaFree(kv.second.d_nunits);
   }
   cudaFree(B->d_sys);
   cudaFree(B->d_state);
   cudaFree(B->d_red);
   cudaFree(B->d_head);
-  cudaFree(B->d_args);
   cudaFreeHost(B->h_sys);
   cudaFreeHost(B->h_state);
-  cudaFreeHost(B->h_args);
   delete B;
 }
 
@@ -590,14 +228,10 @@ static rpcg_status batch_run(rpcg_batch_t B, const double* const* b, double* con
   if (st != RPCG_OK) return st;
   for (int i = 0; i < B->count; i++) {
     rpcg_matrix_t A = B->mats[i];
-    B->h_sys[i] = SysDev{A->m, b[i], x[i], A->r, A->d, A->w, A->inv};
+    double* hist = o.history ? o.history + (size_t)i * (o.max_iter + 1) : nullptr;
+    B->h_sys[i] = SysDev{A->m, b[i], x[i], A->r, A->d, A->w, A->inv, hist, o.tol, o.max_iter, 0};
   }
-  B->h_args->history = o.history;
-  B->h_args->tol = o.tol;
-  B->h_args->max_iter = o.max_iter;
-  B->h_args->count = B->count;
   RPCG_CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys, B->count * sizeof(SysDev), cudaMemcpyHostToDevice, s));
-  RPCG_CUDA_TRY(cudaMemcpyAsync(B->d_args, B->h_args, sizeof(BatchArgs), cudaMemcpyHostToDevice, s));
   RPCG_CUDA_TRY(cudaGraphLaunch(e, s));
   return RPCG_OK;
 }
@@ -626,10 +260,8 @@ rpcg_status rpcg_batch_create(rpcg_batch_t* out, int32_t count, const rpcg_matri
   if (e == cudaSuccess) e = cudaMalloc(&B->d_state, count * sizeof(SysState));
   if (e == cudaSuccess) e = cudaMalloc(&B->d_red, count * sizeof(SysRed));
   if (e == cudaSuccess) e = cudaMalloc(&B->d_head, sizeof(BatchScratchHead));
-  if (e == cudaSuccess) e = cudaMalloc(&B->d_args, sizeof(BatchArgs));
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_sys, count * sizeof(SysDev));
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_state, count * sizeof(SysState));
-  if (e == cudaSuccess) e = cudaMallocHost(&B->h_args, sizeof(BatchArgs));
   if (e == cudaSuccess) e = cudaMemset(B->d_red, 0, count * sizeof(SysRed));
   if (e != cudaSuccess) {
     cudaGetLastError();

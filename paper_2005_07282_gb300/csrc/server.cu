@@ -1,0 +1,569 @@
+// Serving loop: continuous batching of PCG solve requests on one GPU.
+//
+// Requests (CSR + b in host memory) enter a FIFO queue.  A scheduler thread
+// owns the GPU side: it admits requests into a fixed table of slots while a
+// slot is free and the device bytes in use stay within the HBM budget,
+// keeps every matrix it has seen on the device in an LRU cache (requests
+// naming the same host arrays share one device copy; each slot has its own
+// b, x and Krylov vectors), runs the set-up pass for newly admitted
+// systems, and then a chunk of kChunk iterations of the batched passes over
+// every system still iterating.  Between chunks it retires the systems that
+// stopped (copying x back to the host) and admits new requests, so work that
+// arrives while others run joins the batch at the next chunk boundary.
+//
+// Each system goes through exactly the arithmetic of rpcg_solve with the
+// exact dots, so its result is bit-identical to solving it alone, whatever
+// else shares the GPU with it.
+#include <algorithm>
+#include <chrono>
+#include <cstring>
+#include <set>
+#include <condition_variable>
+#include <deque>
+#include <list>
+#include <map>
+#include <mutex>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include "batch.cuh"
+#include "host.h"
+
+namespace rpcg {
+
+constexpr int kChunk = 16;          // iterations between scheduling decisions
+constexpr int kServeTile = 8192;    // rows per work unit
+constexpr int kServeBlock = 128;
+
+static double now_us() {
+  using namespace std::chrono;
+  return (double)duration_cast<nanoseconds>(steady_clock::now().time_since_epoch()).count() * 1e-3;
+}
+
+}  // namespace rpcg
+
+struct rpcg_server_s {
+  struct Req {
+    uint64_t ticket;
+    int n, nnz;
+    const int* rowptr;
+    const int* col;
+    const double* val;
+    const double* b;
+    const double* x0;
+    double tol;
+    int max_iter;
+    double t_submit;
+  };
+  struct Done {
+    rpcg_result res;
+    std::vector<double> x;
+    double queue_us, service_us;
+  };
+  using MatKey = std::tuple<const void*, const void*, const void*, int, int>;
+  struct Mat {
+    rpcg_matrix_t h = nullptr;
+    size_t bytes = 0;
+    int users = 0;
+    uint64_t last_use = 0;
+  };
+  struct Slot {
+    bool used = false;
+    Req req{};
+    double t_admit = 0;
+    MatKey key{};
+    double* buf = nullptr;  // b, x, r, d, w, inv (6 n doubles)
+    size_t bytes = 0;
+  };
+
+  int device = 0;
+  size_t budget = 0;
+  int max_slots = 0;
+  cudaStream_t stream = nullptr;
+  std::thread worker;
+  std::mutex mu;
+  std::condition_variable cv_work, cv_done;
+  bool stop = false;
+  uint64_t next_ticket = 1;
+  std::deque<Req> queue;
+  std::unordered_map<uint64_t, Done> done;
+  std::map<uint64_t, int> pending;  // tickets not yet completed (queued or running)
+
+  // scheduler thread only
+  std::map<MatKey, Mat> mats;
+  std::vector<Slot> slots;
+  size_t used_bytes = 0;
+  uint64_t clock = 0;
+  rpcg::SysDev* d_sys = nullptr;
+  rpcg::SysDev* h_sys = nullptr;
+  rpcg::SysState* d_state = nullptr;
+  rpcg::SysState* h_state = nullptr;
+  rpcg::SysRed* d_red = nullptr;
+  rpcg::BatchScratchHead* d_head = nullptr;
+  rpcg::Unit* d_units = nullptr;
+  rpcg::Unit* d_setup_units = nullptr;
+  int* d_unit_count = nullptr;
+  int* d_counts = nullptr;  // [2]: running units, set-up units
+  int* h_counts = nullptr;
+  double* d_partials = nullptr;
+  int* d_list = nullptr;
+  int unit_cap = 0;
+  int grid_setup = 1, grid_a = 1, grid_b = 1, grid_c = 1, grid_q = 1;
+
+  // statistics
+  uint64_t n_completed = 0, n_failed = 0, n_chunks = 0;
+};
+
+namespace rpcg {
+
+static size_t slot_bytes(int n) { return (size_t)6 * (size_t)(n > 0 ? n : 1) * sizeof(double); }
+
+// device bytes of a matrix handle built from (n, nnz): SELL-32 values and
+// columns (with slice padding, estimated at 5%), row pointers, slice
+// offsets, its own vectors (6 n doubles) and reduction scratch
+static size_t mat_bytes(int n, int nnz) {
+  return (size_t)((double)nnz * 12.0 * 1.05) + (size_t)4 * (n + 1) + (size_t)8 * (n / 32 + 2) + slot_bytes(n) +
+         (size_t)(256 << 10);
+}
+
+static void complete(rpcg_server_t S, uint64_t ticket, const rpcg_result& res, std::vector<double>&& x, double qus,
+                     double sus) {
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto& d = S->done[ticket];
+  d.res = res;
+  d.x = std::move(x);
+  d.queue_us = qus;
+  d.service_us = sus;
+  S->pending.erase(ticket);
+  if (res.status < 0) S->n_failed++;
+  S->n_completed++;
+  S->cv_done.notify_all();
+}
+
+static void fail_req(rpcg_server_t S, const rpcg_server_s::Req& r, int status, double t_admit) {
+  rpcg_result res{0, status, 0.0, 0.0, 0, 0};
+  complete(S, r.ticket, res, {}, t_admit - r.t_submit, now_us() - t_admit);
+}
+
+// Evict cached matrices nobody uses, least recently used first, until
+// `need` more bytes fit.  Returns whether they fit; the evicted handles are
+// appended to `victims` (destroyed by the caller outside the queue lock).
+static bool make_room(rpcg_server_t S, size_t need, std::vector<rpcg_matrix_t>& victims) {
+  while (S->used_bytes + need > S->budget) {
+    auto victim = S->mats.end();
+    for (auto it = S->mats.begin(); it != S->mats.end(); ++it) {
+      if (it->second.users == 0 && (victim == S->mats.end() || it->second.last_use < victim->second.last_use)) victim = it;
+    }
+    if (victim == S->mats.end()) return false;
+    victims.push_back(victim->second.h);
+    S->used_bytes -= victim->second.bytes;
+    S->mats.erase(victim);
+  }
+  return true;
+}
+
+template <class F>
+static cudaError_t launch_check(F f) {
+  f();
+  return cudaGetLastError();
+}
+
+static void serve_loop(rpcg_server_t S) {
+  cudaSetDevice(S->device);
+  cudaStream_t s = S->stream;
+  SysDev* sys = S->d_sys;
+  SysState* sst = S->d_state;
+  SysRed* red = S->d_red;
+  BatchScratchHead* head = S->d_head;
+  int* d_nrun = S->d_counts;
+  int* d_nsetup = S->d_counts + 1;
+  std::vector<int> running;  // slots being iterated
+  for (;;) {
+    // ---- admission (FIFO: stop at the first request that does not fit yet).
+    // A cached matrix is pinned (users + 1) as soon as a request naming it is
+    // admitted; a matrix still to be created is reserved once per round.
+    std::vector<std::pair<int, rpcg_server_s::Req>> admitted;
+    std::vector<rpcg_matrix_t> victims;
+    std::set<rpcg_server_s::MatKey> creating;
+    {
+      std::unique_lock<std::mutex> lock(S->mu);
+      if (running.empty() && S->queue.empty()) {
+        if (S->stop) break;
+        S->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+        if (S->queue.empty()) continue;
+      }
+      while (!S->queue.empty()) {
+        int free_slot = -1;
+        for (int i = 0; i < S->max_slots; i++) {
+          bool taken = S->slots[i].used;
+          for (auto& a : admitted) taken |= a.first == i;
+          if (!taken) {
+            free_slot = i;
+            break;
+          }
+        }
+        if (free_slot < 0) break;
+        const rpcg_server_s::Req r = S->queue.front();
+        const rpcg_server_s::MatKey key{r.rowptr, r.col, r.val, r.n, r.nnz};
+        const bool cached = S->mats.count(key) > 0;
+        const bool known = cached || creating.count(key) > 0;
+        const size_t need = slot_bytes(r.n) + (known ? 0 : mat_bytes(r.n, r.nnz));
+        if (slot_bytes(r.n) + mat_bytes(r.n, r.nnz) > S->budget) {
+          S->queue.pop_front();
+          S->pending.erase(r.ticket);
+          auto& d = S->done[r.ticket];
+          d.res = rpcg_result{0, RPCG_ERR_OOM, 0.0, 0.0, 0, 0};
+          d.queue_us = now_us() - r.t_submit;
+          d.service_us = 0.0;
+          S->n_failed++;
+          S->n_completed++;
+          S->cv_done.notify_all();
+          continue;
+        }
+        if (cached) S->mats[key].users++;  // pinned from now on
+        if (!make_room(S, need, victims)) {
+          if (cached) S->mats[key].users--;
+          break;
+        }
+        S->queue.pop_front();
+        S->used_bytes += need;  // the slot, and the matrix when it is new
+        if (!known) creating.insert(key);
+        admitted.push_back({free_slot, r});
+      }
+    }
+    for (rpcg_matrix_t h : victims) rpcg_destroy(h);
+    // ---- set up the admitted requests
+    std::vector<int> fresh;
+    for (auto& a : admitted) {
+      const int si = a.first;
+      const rpcg_server_s::Req& r = a.second;
+      const double t_admit = now_us();
+      const rpcg_server_s::MatKey key{r.rowptr, r.col, r.val, r.n, r.nnz};
+      auto it = S->mats.find(key);
+      if (it == S->mats.end()) {
+        // first request of this round naming the matrix: create it (its
+        // bytes were reserved at admission)
+        rpcg_matrix_t h = nullptr;
+        const rpcg_status cs = rpcg_create(&h, r.n, r.nnz, r.rowptr, r.col, r.val, 0, s);
+        if (cs != RPCG_OK) {
+          S->used_bytes -= slot_bytes(r.n) + mat_bytes(r.n, r.nnz);
+          creating.erase(key);
+          fail_req(S, r, cs, t_admit);
+          continue;
+        }
+        rpcg_server_s::Mat m;
+        m.h = h;
+        m.bytes = mat_bytes(r.n, r.nnz);
+        it = S->mats.emplace(key, m).first;
+        it->second.users++;
+      } else if (creating.count(key)) {
+        it->second.users++;  // created earlier in this round for another request
+      }
+      // (a matrix cached before this round was pinned at admission)
+      it->second.last_use = ++S->clock;
+      rpcg_server_s::Slot& sl = S->slots[si];
+      sl.used = true;
+      sl.req = r;
+      sl.t_admit = t_admit;
+      sl.key = key;
+      sl.bytes = slot_bytes(r.n);
+      const size_t nb = (size_t)(r.n > 0 ? r.n : 1) * sizeof(double);
+      cudaError_t e = cudaMallocAsync((void**)&sl.buf, 6 * nb, s);
+      double* B = sl.buf;
+      const int n = r.n;
+      if (e == cudaSuccess && n) e = cudaMemcpyAsync(B, r.b, nb, cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && n) {
+        e = r.x0 ? cudaMemcpyAsync(B + n, r.x0, nb, cudaMemcpyHostToDevice, s) : cudaMemsetAsync(B + n, 0, nb, s);
+      }
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (sl.buf) cudaFreeAsync(sl.buf, s);
+        sl.buf = nullptr;
+        sl.used = false;
+        it->second.users--;
+        S->used_bytes -= sl.bytes;
+        fail_req(S, r, RPCG_ERR_CUDA, t_admit);
+        continue;
+      }
+      const rpcg_matrix_t h = it->second.h;
+      S->h_sys[si] = SysDev{h->m, B, B + n, B + 2 * (size_t)n, B + 3 * (size_t)n, B + 4 * (size_t)n,
+                            B + 5 * (size_t)n, nullptr, r.tol, r.max_iter, 0};
+      fresh.push_back(si);
+    }
+    // ---- upload the system table and unit lists; run set-up and a chunk
+    bool ok = true;
+    if (!fresh.empty() || !running.empty()) {
+      std::vector<Unit> units, setup_units;
+      std::vector<int> counts(S->max_slots, 0);
+      for (int si : fresh) running.push_back(si);
+      for (int si : running) {
+        const int n = S->slots[si].req.n;
+        const bool is_new = std::find(fresh.begin(), fresh.end(), si) != fresh.end();
+        for (int r0 = 0; r0 < n; r0 += kServeTile) {
+          const Unit u{si, r0, std::min(n, r0 + kServeTile)};
+          units.push_back(u);
+          if (is_new) setup_units.push_back(u);
+          counts[si]++;
+        }
+      }
+      if ((int)units.size() > S->unit_cap) {
+        // more rows than the unit table holds: cannot happen within the budget
+        // (unit_cap is sized from it), but never overrun the table
+        units.resize(S->unit_cap);
+        ok = false;
+      }
+      S->h_counts[0] = (int)units.size();
+      S->h_counts[1] = (int)setup_units.size();
+      cudaError_t e = cudaSuccess;
+      if (!fresh.empty()) {
+        for (int si : fresh)
+          e = e == cudaSuccess ? cudaMemcpyAsync(S->d_sys + si, S->h_sys + si, sizeof(SysDev), cudaMemcpyHostToDevice, s) : e;
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(S->d_list, fresh.data(), fresh.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+      }
+      if (e == cudaSuccess && !units.empty())
+        e = cudaMemcpyAsync(S->d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess && !setup_units.empty())
+        e = cudaMemcpyAsync(S->d_setup_units, setup_units.data(), setup_units.size() * sizeof(Unit),
+                            cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->d_unit_count, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+      if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_counts, S->h_counts, 2 * sizeof(int), cudaMemcpyHostToDevice, s);
+      Unit* uall = S->d_units;
+      Unit* unew = S->d_setup_units;
+      int* ucount = S->d_unit_count;
+      double* part = S->d_partials;
+      constexpr int B = kServeBlock;
+      if (e == cudaSuccess && !fresh.empty()) {
+        e = launch_check([&] {
+          k_b_init_list<<<1, 256, 0, s>>>(S->d_list, (int)fresh.size(), sys, sst, head);
+          k_b_inv_q<<<S->grid_q, B, 0, s>>>(sys, unew, d_nsetup, sst);
+          k_b_setup<RPCG_EXBLAS, B><<<S->grid_setup, B, b_smem<RPCG_EXBLAS>(3), s>>>(sys, unew, d_nsetup, ucount, sst,
+                                                                                  red, part, head);
+        });
+      }
+      if (e == cudaSuccess && !units.empty()) {
+        e = launch_check([&] {
+          for (int k = 0; k < kChunk; k++) {
+            k_b_pass_a<RPCG_EXBLAS, B><<<S->grid_a, B, b_smem<RPCG_EXBLAS>(1), s>>>(sys, uall, d_nrun, ucount, sst, red,
+                                                                                 part, head);
+            k_b_pass_b<RPCG_EXBLAS, B><<<S->grid_b, B, b_smem<RPCG_EXBLAS>(2), s>>>(sys, uall, d_nrun, ucount, sst, red,
+                                                                                 part, head);
+            k_b_pass_c<B><<<S->grid_c, B, 0, s>>>(sys, uall, d_nrun, sst);
+            k_b_retire<<<(S->max_slots + 255) / 256, 256, 0, s>>>(sst, S->max_slots, head);
+          }
+        });
+      }
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(S->h_state, S->d_state, S->max_slots * sizeof(SysState), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+      if (e != cudaSuccess) ok = false;
+      S->n_chunks++;
+    }
+    // ---- retire the systems that stopped (or everything, after an error)
+    std::vector<int> still;
+    for (int si : running) {
+      rpcg_server_s::Slot& sl = S->slots[si];
+      const SysState& h = S->h_state[si];
+      if (ok && h.active) {
+        still.push_back(si);
+        continue;
+      }
+      const int n = sl.req.n;
+      std::vector<double> x((size_t)n);
+      rpcg_result res{h.iter, h.status, h.rel, h.tau, 0, 0};
+      if (!ok) res.status = RPCG_ERR_CUDA;
+      if (ok && h.bzero) std::fill(x.begin(), x.end(), 0.0);
+      else if (n && cudaMemcpy(x.data(), sl.buf + n, (size_t)n * sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+        res.status = RPCG_ERR_CUDA;
+      if (res.status == RPCG_OK && !(h.rel < sl.req.tol)) res.status = RPCG_NOT_CONVERGED;
+      cudaFreeAsync(sl.buf, s);
+      sl.buf = nullptr;
+      sl.used = false;
+      S->mats[sl.key].users--;
+      S->used_bytes -= sl.bytes;
+      complete(S, sl.req.ticket, res, std::move(x), sl.t_admit - sl.req.t_submit, now_us() - sl.t_admit);
+    }
+    running.swap(still);
+  }
+}
+
+}  // namespace rpcg
+
+using namespace rpcg;
+
+extern "C" {
+
+rpcg_status rpcg_server_create(rpcg_server_t* out, size_t hbm_budget_bytes, int32_t max_slots) {
+  clear_error();
+  RPCG_CHECK_ARG(out != nullptr, "out is NULL");
+  *out = nullptr;
+  RPCG_CHECK_ARG(max_slots >= 1 && max_slots <= 4096, "max_slots must be 1..4096");
+  RPCG_CHECK_ARG(hbm_budget_bytes >= ((size_t)1 << 20), "the budget must be at least 1 MiB");
+  rpcg_server_t S = new rpcg_server_s();
+  S->budget = hbm_budget_bytes;
+  S->max_slots = max_slots;
+  S->slots.resize(max_slots);
+  cudaGetDevice(&S->device);
+  // unit table: every running row belongs to a slot whose vectors count
+  // against the budget (48 bytes per row), so this bounds the units
+  const size_t cap = (size_t)max_slots + hbm_budget_bytes / (48 * (size_t)kServeTile) + 64;
+  S->unit_cap = (int)std::min<size_t>(cap, (size_t)1 << 22);
+  cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sys, max_slots * sizeof(SysDev));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_sys, max_slots * sizeof(SysDev));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_state, max_slots * sizeof(SysState));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_state, max_slots * sizeof(SysState));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_red, max_slots * sizeof(SysRed));
+  if (e == cudaSuccess) e = cudaMemset(S->d_red, 0, max_slots * sizeof(SysRed));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_head, sizeof(BatchScratchHead));
+  if (e == cudaSuccess) e = cudaMemset(S->d_head, 0, sizeof(BatchScratchHead));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_units, (size_t)S->unit_cap * sizeof(Unit));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_setup_units, (size_t)S->unit_cap * sizeof(Unit));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_unit_count, max_slots * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, 2 * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_partials, (size_t)S->unit_cap * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_list, max_slots * sizeof(int));
+  if (e == cudaSuccess) {
+    std::memset(S->h_state, 0, max_slots * sizeof(SysState));
+    e = cudaMemset(S->d_state, 0, max_slots * sizeof(SysState));
+  }
+  constexpr int B = kServeBlock;
+  auto occ = [&](const void* f, size_t smem) {
+    int o = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&o, f, B, smem) != cudaSuccess || o < 1) o = 1;
+    return sm_count() * o;
+  };
+  if (e == cudaSuccess) {
+    cudaFuncSetAttribute((const void*)k_b_setup<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)b_smem<RPCG_EXBLAS>(3));
+    cudaFuncSetAttribute((const void*)k_b_pass_a<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)b_smem<RPCG_EXBLAS>(1));
+    cudaFuncSetAttribute((const void*)k_b_pass_b<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)b_smem<RPCG_EXBLAS>(2));
+    S->grid_setup = occ((const void*)k_b_setup<RPCG_EXBLAS, B>, b_smem<RPCG_EXBLAS>(3));
+    S->grid_a = occ((const void*)k_b_pass_a<RPCG_EXBLAS, B>, b_smem<RPCG_EXBLAS>(1));
+    S->grid_b = occ((const void*)k_b_pass_b<RPCG_EXBLAS, B>, b_smem<RPCG_EXBLAS>(2));
+    S->grid_c = occ((const void*)k_b_pass_c<B>, 0);
+    S->grid_q = occ((const void*)k_b_inv_q, 0);
+    e = cudaGetLastError();
+  }
+  if (e != cudaSuccess) {
+    set_error("rpcg_server_create: %s", cudaGetErrorString(e));
+    rpcg_server_destroy(S);
+    return e == cudaErrorMemoryAllocation ? RPCG_ERR_OOM : RPCG_ERR_CUDA;
+  }
+  S->worker = std::thread(serve_loop, S);
+  *out = S;
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_server_submit(rpcg_server_t S, int32_t n, int32_t nnz, const int32_t* rowptr, const int32_t* col,
+                               const double* val, const double* b, const double* x0, int32_t v, const rpcg_opts* o,
+                               uint64_t* ticket) {
+  clear_error();
+  RPCG_CHECK_ARG(S != nullptr && ticket != nullptr, "server or ticket is NULL");
+  RPCG_CHECK_ARG(v == RPCG_EXBLAS, "the serving loop runs the exblas variant");
+  RPCG_CHECK_ARG(n >= 0 && nnz >= 0 && rowptr != nullptr && (n == 0 || b != nullptr), "bad request arrays");
+  RPCG_CHECK_ARG(nnz == 0 || (col != nullptr && val != nullptr), "col or val is NULL");
+  rpcg_opts opt;
+  if (o) opt = *o;
+  else rpcg_opts_default(&opt);
+  RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0), "bad tol or max_iter");
+  rpcg_server_s::Req r{};
+  r.n = n;
+  r.nnz = nnz;
+  r.rowptr = rowptr;
+  r.col = col;
+  r.val = val;
+  r.b = b;
+  r.x0 = x0;
+  r.tol = opt.tol;
+  r.max_iter = opt.max_iter;
+  r.t_submit = now_us();
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    RPCG_CHECK_ARG(!S->stop, "server is shutting down");
+    r.ticket = S->next_ticket++;
+    S->queue.push_back(r);
+    S->pending[r.ticket] = 1;
+    *ticket = r.ticket;
+  }
+  S->cv_work.notify_one();
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_server_wait(rpcg_server_t S, uint64_t ticket, double* x_host, rpcg_result* res,
+                             rpcg_server_timing* timing, int64_t timeout_us) {
+  clear_error();
+  RPCG_CHECK_ARG(S != nullptr && res != nullptr, "server or res is NULL");
+  std::unique_lock<std::mutex> lock(S->mu);
+  auto ready = [&] { return S->done.count(ticket) > 0 || (S->pending.count(ticket) == 0); };
+  if (timeout_us < 0) S->cv_done.wait(lock, ready);
+  else if (!S->cv_done.wait_for(lock, std::chrono::microseconds(timeout_us), ready)) {
+    set_error("rpcg_server_wait: ticket %llu not done within %lld us", (unsigned long long)ticket, (long long)timeout_us);
+    return RPCG_ERR_TIMEOUT;
+  }
+  auto it = S->done.find(ticket);
+  if (it == S->done.end()) {
+    set_error("rpcg_server_wait: unknown ticket %llu", (unsigned long long)ticket);
+    return RPCG_ERR_INVALID;
+  }
+  *res = it->second.res;
+  if (x_host && !it->second.x.empty()) std::memcpy(x_host, it->second.x.data(), it->second.x.size() * sizeof(double));
+  if (timing) {
+    timing->queue_us = it->second.queue_us;
+    timing->service_us = it->second.service_us;
+  }
+  S->done.erase(it);
+  return (rpcg_status)res->status;
+}
+
+rpcg_status rpcg_server_stats(rpcg_server_t S, rpcg_server_stats_t* st) {
+  RPCG_CHECK_ARG(S != nullptr && st != nullptr, "NULL argument");
+  std::lock_guard<std::mutex> lock(S->mu);
+  st->completed = S->n_completed;
+  st->failed = S->n_failed;
+  st->queued = S->queue.size();
+  st->chunks = S->n_chunks;
+  st->bytes_in_use = S->used_bytes;
+  st->matrices_cached = S->mats.size();
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_server_destroy(rpcg_server_t S) {
+  clear_error();
+  if (!S) return RPCG_OK;
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    S->stop = true;
+  }
+  S->cv_work.notify_all();
+  if (S->worker.joinable()) S->worker.join();
+  cudaSetDevice(S->device);
+  if (S->stream) cudaStreamSynchronize(S->stream);
+  for (auto& sl : S->slots)
+    if (sl.buf) cudaFree(sl.buf);
+  for (auto& kv : S->mats) rpcg_destroy(kv.second.h);
+  cudaFree(S->d_sys);
+  cudaFreeHost(S->h_sys);
+  cudaFree(S->d_state);
+  cudaFreeHost(S->h_state);
+  cudaFree(S->d_red);
+  cudaFree(S->d_head);
+  cudaFree(S->d_units);
+  cudaFree(S->d_setup_units);
+  cudaFree(S->d_unit_count);
+  cudaFree(S->d_counts);
+  cudaFreeHost(S->h_counts);
+  cudaFree(S->d_partials);
+  cudaFree(S->d_list);
+  if (S->stream) cudaStreamDestroy(S->stream);
+  delete S;
+  return RPCG_OK;
+}
+
+}  // extern "C"

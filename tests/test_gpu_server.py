@@ -1,0 +1,104 @@
+"""The serving loop: results are bit-identical alone and in the mix, work
+that arrives while other solves run joins them (continuous batching), and
+admission respects the HBM budget."""
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import synth
+from conftest import bits
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(rpcg, cuda, A, b, x0=None, tol=1e-8):
+    import torch
+    M = rpcg.Matrix.from_csr(A)
+    x = torch.zeros(A.n, dtype=torch.float64, device=cuda) if x0 is None else torch.from_numpy(x0.copy()).to(cuda)
+    r = M.solve(torch.from_numpy(b).to(cuda), x, variant="exblas", tol=tol, max_iter=2000)
+    M.close()
+    return r, x.cpu().numpy()
+
+
+def test_server_results_identical_alone_and_in_mix(rpcg, cuda):
+    sides = [6, 11, 16, 9, 6, 20, 11, 3]
+    mats = {s: synth.poisson7(s) for s in set(sides)}  # repeated sides share one matrix
+    reqs = []
+    for k, s in enumerate(sides):
+        A = mats[s]
+        b = synth.rhs_uniform(A.n, 300 + k)
+        x0 = synth.uniform_pm1(400 + k, A.n) if k % 3 == 0 else None
+        reqs.append((A, b, x0))
+    srv = rpcg.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    tickets = [srv.submit(A, b, x0=x0, tol=1e-8, max_iter=2000) for A, b, x0 in reqs]
+    outs = [srv.wait(t, timeout_us=120_000_000) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    assert st["completed"] == len(reqs) and st["failed"] == 0
+    assert st["matrices_cached"] <= len(mats)
+    for (A, b, x0), (x, res) in zip(reqs, outs):
+        ra, xa = _alone(rpcg, cuda, A, b, x0)
+        assert res["status"] == ra["status"] == 0
+        assert res["iterations"] == ra["iterations"]
+        assert bits([res["relres"]])[0] == bits([ra["relres"]])[0]
+        assert np.array_equal(bits(x), bits(xa))
+        assert res["queue_us"] >= 0 and res["service_us"] > 0
+
+
+def test_server_admits_work_while_others_run(rpcg, cuda):
+    """A long solve is running; short requests submitted afterwards finish
+    before it does, so they were admitted alongside it."""
+    big = synth.poisson27(48)
+    b_big = synth.rhs_uniform(big.n, 9)
+    small = synth.poisson7(8)
+    srv = rpcg.Server(hbm_budget_bytes=4 << 30, max_slots=8)
+    t_big = srv.submit(big, b_big, tol=1e-12, max_iter=2000)
+    time.sleep(0.02)
+    t_small = [srv.submit(small, synth.rhs_uniform(small.n, 50 + k), tol=1e-8) for k in range(5)]
+    done_order = []
+    lock = threading.Lock()
+
+    def waiter(t):
+        x, r = srv.wait(t, timeout_us=120_000_000)
+        with lock:
+            done_order.append(t)
+
+    ths = [threading.Thread(target=waiter, args=(t,)) for t in [t_big] + t_small]
+    for th in ths:
+        th.start()
+    for th in ths:
+        th.join()
+    srv.close()
+    assert done_order[-1] == t_big, done_order
+
+
+def test_server_budget_and_errors(rpcg, cuda):
+    # a 40^3 system needs ~9 MB for its matrix and ~3 MB for its vectors, a
+    # 32^3 one ~5 + ~1.6 MB: a 20 MB budget holds only part of the requests at
+    # once, so the rest wait for slots and memory, reuse or evict matrices
+    A = synth.poisson7(40)
+    other = synth.poisson7(32)
+    srv = rpcg.Server(hbm_budget_bytes=20 << 20, max_slots=4)
+    ts = [srv.submit(A if k % 2 == 0 else other, synth.rhs_uniform((A if k % 2 == 0 else other).n, k)) for k in range(6)]
+    for t in ts:
+        x, r = srv.wait(t, timeout_us=120_000_000)
+        assert r["status"] == 0
+    st = srv.stats()
+    assert st["bytes_in_use"] <= 20 << 20
+    # a request larger than the whole budget fails at once with OOM
+    huge = synth.poisson7(80)
+    th = srv.submit(huge, synth.rhs_uniform(huge.n, 1))
+    x, r = srv.wait(th, timeout_us=60_000_000)
+    assert r["status"] == rpcg.ERR_OOM
+    # an unknown ticket is rejected; a short wait on a long solve times out
+    with pytest.raises(rpcg.RpcgError):
+        srv.wait(987654, timeout_us=1000)
+    big = synth.poisson7(32)
+    tb = srv.submit(big, synth.rhs_uniform(big.n, 3), tol=1e-14, max_iter=2000)
+    with pytest.raises(TimeoutError):
+        srv.wait(tb, timeout_us=1)
+    x, r = srv.wait(tb, timeout_us=120_000_000)
+    assert r["status"] in (0, rpcg.NOT_CONVERGED)
+    srv.close()
