@@ -46,11 +46,15 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--side", type=int, default=256, help="grid side of the 27-point Poisson workload")
+    ap.add_argument("--side", type=int, default=256, help="grid side of the Poisson workload")
+    ap.add_argument("--stencil", type=int, choices=[7, 27], default=27, help="7- or 27-point Poisson")
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip the plain/fpe/dot/e2e side measurements")
+    ap.add_argument("--serve", type=float, default=0.0, metavar="SECONDS",
+                    help="only the serving workload: Poisson arrivals of 7-point systems, side log-uniform in [16,128]")
+    ap.add_argument("--rate", type=float, default=2000.0, help="offered arrival rate for --serve (requests/s)")
     ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
                     help="only the batched workload: COUNT variable-diffusion systems, s ~ U{8..64}, tol 1e-10")
     ap.add_argument("--dot-only", type=int, default=0, metavar="LOG2N",
@@ -68,8 +72,8 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def workload(side):
-    A = synth.poisson27(side)
+def workload(side, stencil=27):
+    A = synth.poisson27(side) if stencil == 27 else synth.poisson7(side)
     xt = synth.poisson_rhs_xtrue(A.n, synth.BASE_SEED + 2)
     return A, xt
 
@@ -156,7 +160,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     import oracle
-    A, xt = workload(args.side)
+    A, xt = workload(args.side, args.stencil)
     b = oracle.spmv(A, xt, nthreads=oracle.default_threads())
     per_step = 2
     for _ in range(args.warmup):
@@ -171,7 +175,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"poisson27_{args.side}", "n": A.n, "nnz": A.nnz, "tol": args.tol,
+            "config": {"workload": f"poisson{args.stencil}_{args.side}", "n": A.n, "nnz": A.nnz, "tol": args.tol,
                        "step": f"{per_step} PCG iterations of the oracle (set-up excluded from the time)"},
             "cpu_baseline": {"value": v, "unit": "iters/s", "cores": nt, "kind": "oracle",
                              "sample": f"{args.steps} x {per_step} iterations of the exact-dot PCG"},
@@ -215,7 +219,7 @@ def gpu_arm(args, rank, world, local_rank):
         return float(t.item())
 
     # ---- inputs (host CSR in pinned memory for the end-to-end leg)
-    A, xt = workload(args.side)
+    A, xt = workload(args.side, args.stencil)
     n, nnz = A.n, A.nnz
     M = P.Matrix.from_csr(A)
     d_xt = torch.from_numpy(xt).to(dev)
@@ -363,7 +367,7 @@ def gpu_arm(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"poisson27_{args.side} exblas", "n": n, "nnz": nnz, "tol": args.tol,
+                "config": {"workload": f"poisson{args.stencil}_{args.side} exblas", "n": n, "nnz": nnz, "tol": args.tol,
                            "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
                            "solve_status": status, "step": "one complete solve from x0 = 0",
                            "l2": "inputs larger than L2 (CSR 5.46 GB streamed every iteration)",
@@ -478,8 +482,131 @@ def batch_arm(args):
                       "generation_s": gen_s}), flush=True)
 
 
+def serve_arm(args):
+    """--serve SECONDS: the serving workload.  Requests are 7-point Poisson
+    systems with side log-uniform in [16, 128] and b ~ U[-1, 1], exblas, tol
+    1e-8, under a 64 GB HBM budget.  Three phases: capacity (closed loop with
+    every slot busy), open-loop Poisson arrivals at 80% of that capacity, and
+    open-loop arrivals at the offered rate.  Reports solves/s and p50/p99 of
+    queueing, service and total latency per phase, and checks a sample of
+    results bit for bit against solving each system alone."""
+    import threading
+
+    import torch
+
+    import paper_2005_07282_gb300 as P
+    from paper_2005_07282_gb300 import build as B
+    B.build()
+    dev = torch.device("cuda", 0)
+    seed = synth.BASE_SEED + 4
+    rng = np.random.default_rng(seed)
+    t0 = time.perf_counter()
+    mats = {s: synth.poisson7(s) for s in range(16, 129)}
+    pool = synth.uniform_pm1(synth.stream_seed(seed, 1), 128 ** 3 + (1 << 20))
+    gen_s = time.perf_counter() - t0
+
+    def make_request():
+        side = int(round(np.exp(rng.uniform(np.log(16), np.log(128)))))
+        A = mats[side]
+        off = int(rng.integers(0, 1 << 20))
+        return A, pool[off:off + A.n]
+
+    srv = P.Server(hbm_budget_bytes=64 << 30, max_slots=256)
+
+    def pct(v, q):
+        return float(np.percentile(np.asarray(v), q)) if v else None
+
+    def phase(duration, rate=None, closed=0):
+        """Open loop at `rate` for `duration` s, or a closed loop keeping
+        `closed` requests in flight.  Returns throughput and latencies."""
+        lat, qs, ss, statuses, sample = [], [], [], [], []
+        lock = threading.Lock()
+        done_count = [0]
+        tickets = []
+        t_start = time.perf_counter()
+        stop_at = t_start + duration
+
+        def collect(t, ts_submit, req):
+            x, r = srv.wait(t)
+            now = time.perf_counter()
+            with lock:
+                lat.append((now - ts_submit) * 1e6)
+                qs.append(r["queue_us"])
+                ss.append(r["service_us"])
+                statuses.append(r["status"])
+                done_count[0] += 1
+                if len(sample) < 12 and req[0].n <= 64 ** 3:
+                    sample.append((req, x.copy(), r["iterations"]))
+
+        collectors = []
+        if closed:
+            inflight = threading.Semaphore(closed)
+
+            def run_one(req, ts):
+                try:
+                    t = srv.submit(req[0], req[1], tol=1e-8, max_iter=5000)
+                    collect(t, ts, req)
+                finally:
+                    inflight.release()
+
+            while time.perf_counter() < stop_at:
+                inflight.acquire()
+                req = make_request()
+                th = threading.Thread(target=run_one, args=(req, time.perf_counter()))
+                th.start()
+                collectors.append(th)
+        else:
+            next_t = t_start
+            while True:
+                next_t += rng.exponential(1.0 / rate)
+                if next_t >= stop_at:
+                    break
+                delay = next_t - time.perf_counter()
+                if delay > 0:
+                    time.sleep(delay)
+                req = make_request()
+                ts = time.perf_counter()
+                t = srv.submit(req[0], req[1], tol=1e-8, max_iter=5000)
+                th = threading.Thread(target=collect, args=(t, ts, req))
+                th.start()
+                collectors.append(th)
+        for th in collectors:
+            th.join()
+        wall = time.perf_counter() - t_start
+        return {"requests": done_count[0], "wall_s": wall, "solves_per_s": done_count[0] / wall,
+                "latency_us": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
+                "queue_us": {"p50": pct(qs, 50), "p99": pct(qs, 99)},
+                "service_us": {"p50": pct(ss, 50), "p99": pct(ss, 99)},
+                "statuses": sorted(set(statuses))}, sample
+
+    dur = args.serve
+    cap, sample = phase(dur, closed=256)
+    capacity = cap["solves_per_s"]
+    at80, s2 = phase(dur, rate=0.8 * capacity)
+    offered, s3 = phase(min(dur, 1.0), rate=args.rate)
+    # bit-identity of served results with solving each system alone
+    same = True
+    for (A, b), x, its in (sample + s2)[:16]:
+        M = P.Matrix.from_csr(A)
+        xd = torch.zeros(A.n, dtype=torch.float64, device=dev)
+        r = M.solve(torch.from_numpy(np.ascontiguousarray(b)).to(dev), xd, variant="exblas", tol=1e-8, max_iter=5000)
+        same &= r["iterations"] == its and np.array_equal(xd.cpu().numpy().view(np.int64), x.view(np.int64))
+        M.close()
+    st = srv.stats()
+    srv.close()
+    print(json.dumps({"workload": "serving: 7-point Poisson, side log-uniform [16,128], b~U[-1,1], exblas, tol 1e-8, "
+                                  "64 GB budget, 256 slots",
+                      "capacity_closed_loop": cap, "at_80pct_capacity": {"rate": 0.8 * capacity, **at80},
+                      "at_offered_rate": {"rate": args.rate, "arrival_window_s": min(dur, 1.0), **offered},
+                      "bit_identical_to_alone_sample": bool(same), "server_stats": st,
+                      "generation_s": gen_s}), flush=True)
+
+
 def main():
     args = parse()
+    if args.serve:
+        serve_arm(args)
+        return
     if args.batch:
         batch_arm(args)
         return
