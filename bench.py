@@ -95,6 +95,18 @@ def iter_bytes(n, nnz):
     return 12 * nnz + 4 * (n + 1) + 88 * n
 
 
+def reduce_over_ranks(v, op, device):
+    """Max or sum of a scalar over the ranks of the default process group
+    (identity without one).  Timings take the max, work counts the sum."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return v
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 class ClockSampler:
     """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
 
@@ -205,18 +217,10 @@ def gpu_arm(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(v, "max", dev)
 
     def sum_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(v, "sum", dev)
 
     # ---- inputs (host CSR in pinned memory for the end-to-end leg)
     A, xt = workload(args.side, args.stencil)
