@@ -48,6 +48,9 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=256, help="grid side of the Poisson workload")
     ap.add_argument("--stencil", type=int, choices=[7, 27], default=27, help="7- or 27-point Poisson")
+    ap.add_argument("--band", type=int, default=0, metavar="BW",
+                    help="use the band matrix of half-bandwidth BW (the paper's performance workload) instead")
+    ap.add_argument("--band-n", type=int, default=4_000_000, help="rows of the band matrix")
     ap.add_argument("--max-iter", type=int, default=5000)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -72,8 +75,11 @@ def hbm_peak():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def workload(side, stencil=27):
-    A = synth.poisson27(side) if stencil == 27 else synth.poisson7(side)
+def workload(side, stencil=27, band=0, band_n=0):
+    if band:
+        A = synth.band(band_n, band)
+    else:
+        A = synth.poisson27(side) if stencil == 27 else synth.poisson7(side)
     xt = synth.poisson_rhs_xtrue(A.n, synth.BASE_SEED + 2)
     return A, xt
 
@@ -83,6 +89,10 @@ def workload(side, stencil=27):
 # 128^3 case / its algorithmic bytes); the kernel streams every matrix entry
 # once, so the full-size launch's traffic is this ratio times its bytes.
 PASS_A_TRAFFIC_RATIO = 701.7 / 710.9
+
+
+def wl_name(args):
+    return f"band_{args.band_n}_bw{args.band}" if args.band else f"poisson{args.stencil}_{args.side}"
 
 
 def pass_a_bytes(n, nnz):
@@ -172,7 +182,7 @@ def reference_arm(args, rank, world):
     if rank != 0:
         return
     import oracle
-    A, xt = workload(args.side, args.stencil)
+    A, xt = workload(args.side, args.stencil, args.band, args.band_n)
     b = oracle.spmv(A, xt, nthreads=oracle.default_threads())
     per_step = 2
     for _ in range(args.warmup):
@@ -187,7 +197,7 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"poisson{args.stencil}_{args.side}", "n": A.n, "nnz": A.nnz, "tol": args.tol,
+            "config": {"workload": wl_name(args), "n": A.n, "nnz": A.nnz, "tol": args.tol,
                        "step": f"{per_step} PCG iterations of the oracle (set-up excluded from the time)"},
             "cpu_baseline": {"value": v, "unit": "iters/s", "cores": nt, "kind": "oracle",
                              "sample": f"{args.steps} x {per_step} iterations of the exact-dot PCG"},
@@ -223,7 +233,7 @@ def gpu_arm(args, rank, world, local_rank):
         return reduce_over_ranks(v, "sum", dev)
 
     # ---- inputs (host CSR in pinned memory for the end-to-end leg)
-    A, xt = workload(args.side, args.stencil)
+    A, xt = workload(args.side, args.stencil, args.band, args.band_n)
     n, nnz = A.n, A.nnz
     M = P.Matrix.from_csr(A)
     d_xt = torch.from_numpy(xt).to(dev)
@@ -303,8 +313,9 @@ def gpu_arm(args, rank, world, local_rank):
         peak, peak_kind = hbm_peak()
         ach = pass_a_bytes(n, nnz) / (a_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz),
-                "traffic_source": "ncu dram bytes of the 128^3 launch scaled by algorithmic bytes",
+                "traffic": (PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz)
+                            if (not args.band and args.stencil == 27) else None),
+                "traffic_source": "ncu dram bytes of the 27-point 128^3 launch scaled by algorithmic bytes",
                 "kernel": "k_pass_a (SpMV + <d,w> exact deposit)",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": pass_a_bytes(n, nnz), "avg_launch_ms": a_ms}
@@ -371,7 +382,7 @@ def gpu_arm(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": f"poisson{args.stencil}_{args.side} exblas", "n": n, "nnz": nnz, "tol": args.tol,
+                "config": {"workload": wl_name(args) + " exblas", "n": n, "nnz": nnz, "tol": args.tol,
                            "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
                            "solve_status": status, "step": "one complete solve from x0 = 0",
                            "l2": "inputs larger than L2 (CSR 5.46 GB streamed every iteration)",

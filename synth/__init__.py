@@ -212,6 +212,35 @@ def diffusion7(s: int, seed: int) -> tuple[CSR, float]:
     return A, sig
 
 
+def band(n: int, bw: int) -> CSR:
+    """Band matrix with half-bandwidth bw: row i holds columns
+    max(0, i-bw) .. min(n-1, i+bw), diagonal 2 bw + 1 and off-diagonals -1
+    (strictly diagonally dominant, so SPD).  The paper's performance runs use
+    a band version of its Poisson matrix (Sec. 5.1) without giving the entry
+    values; these values are this module's choice."""
+    rows = np.arange(n, dtype=np.int64)
+    lo = np.maximum(rows - bw, 0)
+    hi = np.minimum(rows + bw, n - 1)
+    counts = (hi - lo + 1).astype(np.int64)
+    rowptr = np.zeros(n + 1, dtype=np.int64)
+    np.cumsum(counts, out=rowptr[1:])
+    nnz = int(rowptr[-1])
+    if nnz >= 2**31:
+        raise ValueError("too many nonzeros for int32 row pointers")
+    col = np.empty(nnz, dtype=np.int32)
+    val = np.full(nnz, -1.0, dtype=np.float64)
+    # entry k of row i is column lo_i + k
+    for start in range(0, n, 1 << 20):
+        stop = min(n, start + (1 << 20))
+        c = counts[start:stop]
+        base = np.repeat(lo[start:stop] - rowptr[start:stop], c)  # column minus position
+        pos = np.arange(rowptr[start], rowptr[stop], dtype=np.int64)
+        col[rowptr[start]:rowptr[stop]] = (pos + base).astype(np.int32)
+    diag_pos = rowptr[:-1] + (rows - lo)
+    val[diag_pos] = float(2 * bw + 1)
+    return CSR(n, rowptr.astype(np.int32), col, val, f"band_{n}_{bw}")
+
+
 # ---------------------------------------------------------------- dot inputs
 
 def dot_family_a(n: int, seed: int) -> tuple[np.ndarray, np.ndarray]:

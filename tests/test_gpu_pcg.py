@@ -220,3 +220,19 @@ def test_profiled_solve_matches_graph_solve(rpcg, cuda, oracle_lib, variant):
     assert r1["iterations"] == r2["iterations"] == r2["launches"]["A"]
     assert np.array_equal(bits(x1.cpu().numpy()), bits(x2.cpu().numpy()))
     assert r2["pass_ms"]["A"] > 0
+
+
+def test_band_matrix_spmv_and_pcg(rpcg, cuda, oracle_lib):
+    """The band workload (rows of 2 bw + 1 entries) against the oracle."""
+    import torch
+    A = synth.band(3000, 40)
+    x = synth.uniform_pm1(SEED + 11, A.n)
+    M = rpcg.Matrix.from_csr(A)
+    y = M.spmv(_dev(x, cuda)).cpu().numpy()
+    assert np.array_equal(bits(y), bits(oracle_lib.spmv(A, x)))
+    b = oracle_lib.spmv(A, np.ones(A.n))  # the paper's right-hand side: A times a vector of ones
+    ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, tol=1e-8, max_iter=500)
+    xd = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    r = M.solve(_dev(b, cuda), xd, tol=1e-8, max_iter=500)
+    assert r["iterations"] == ref["iterations"] and r["status"] == 0
+    assert np.array_equal(bits(xd.cpu().numpy()), bits(ref["x"]))

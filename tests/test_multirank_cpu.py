@@ -21,6 +21,14 @@ def _free_port():
 
 
 def _worker(rank, world, port, q):
+    try:
+        _work(rank, world, port, q)
+    except BaseException as e:  # report instead of leaving the peer waiting
+        q.put((rank, None, None, f"error: {e!r}"))
+        raise
+
+
+def _work(rank, world, port, q):
     sys.path.insert(0, ROOT)
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
     import torch
@@ -36,7 +44,7 @@ def _worker(rank, world, port, q):
     buf = io.StringIO()
 
     class A:
-        side, stencil, steps, warmup, tol = 6, 7, 1, 1, 1e-8
+        side, stencil, steps, warmup, tol, band, band_n = 6, 7, 1, 1, 1e-8, 0, 0
 
     with contextlib.redirect_stdout(buf):
         bench.reference_arm(A, rank, world)
@@ -52,7 +60,9 @@ def test_two_gloo_ranks():
     procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
     for p in procs:
         p.start()
-    out = [q.get(timeout=180) for _ in procs]
+    out = [q.get(timeout=120) for _ in procs]
+    errors = [o[3] for o in out if o[1] is None]
+    assert not errors, errors
     for p in procs:
         p.join(timeout=60)
         assert p.exitcode == 0
