@@ -176,6 +176,19 @@ rpcg_status rpcg_dot_fpe(int64_t n, const double *a, const double *b, int32_t p,
                          void *stream);
 
 /*
+ * rpcg_eft_twosum / rpcg_eft_twoprod -- the error-free transformations of
+ * Alg. 1 (r = RN(a_i + b_i), s = a_i + b_i - r) and Alg. 2 (r = RN(a_i b_i),
+ * s = fma(a_i, b_i, -r)) applied elementwise.  Finite non-zero elements are
+ * computed exactly on the integer pipe (the FPE dot's arithmetic); zero,
+ * non-finite or out-of-range elements use the FP64 formulas; every output
+ * equals the FP64 algorithm's bit for bit.
+ *   a, b      device arrays of n doubles (inputs); r, s: device outputs.
+ * Asynchronous.
+ */
+rpcg_status rpcg_eft_twosum(int64_t n, const double *a, const double *b, double *r, double *s, void *stream);
+rpcg_status rpcg_eft_twoprod(int64_t n, const double *a, const double *b, double *r, double *s, void *stream);
+
+/*
  * rpcg_dot_plain -- ordinary FP64 dot (fma per element per thread, fixed
  * shuffle/shared-memory tree, then a fixed tree over CTA partials).  The
  * non-reproducible baseline of the paper's "Regular" PCG (Sec. 5.2).

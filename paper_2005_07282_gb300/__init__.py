@@ -29,7 +29,8 @@ EXPORTS = [
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
     "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
     "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
-    "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy",
+    "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_eft_twosum",
+    "rpcg_eft_twoprod",
 ]
 
 
@@ -87,6 +88,8 @@ def lib():
         L.rpcg_dot_exact.argtypes = [i64, P, P, P, P]
         L.rpcg_dot_fpe.argtypes = [i64, P, P, i32, P, P, P]
         L.rpcg_dot_exact_noalloc.argtypes = [i64, P, P, P, P]
+        L.rpcg_eft_twosum.argtypes = [i64, P, P, P, P, P]
+        L.rpcg_eft_twoprod.argtypes = [i64, P, P, P, P, P]
         L.rpcg_batch_create.argtypes = [ctypes.POINTER(P), i32, P]
         L.rpcg_batch_destroy.argtypes = [P]
         L.rpcg_batch_solve.argtypes = [P, P, P, i32, ctypes.POINTER(Opts), P, P]
@@ -167,6 +170,15 @@ def dot_fpe(a, b, p=8, stream=None):
     _check(lib().rpcg_dot_fpe(a.numel(), _dptr(a), _dptr(b), p, ctypes.c_void_p(out.data_ptr()),
                               ctypes.c_void_p(ex.data_ptr()), _stream(stream)), "rpcg_dot_fpe")
     return out, ex
+
+
+def eft(kind, a, b, stream=None):
+    """Elementwise Alg. 1 (kind="twosum") or Alg. 2 (kind="twoprod"): returns (r, s)."""
+    import torch
+    r, s = torch.empty_like(a), torch.empty_like(a)
+    fn = lib().rpcg_eft_twosum if kind == "twosum" else lib().rpcg_eft_twoprod
+    _check(fn(a.numel(), _dptr(a), _dptr(b), _dptr(r), _dptr(s), _stream(stream)), "rpcg_eft_" + kind)
+    return r, s
 
 
 def dot_plain(a, b, stream=None):

@@ -273,6 +273,13 @@ __device__ __forceinline__ void two_prod(double a, double b, double& r, double& 
   s = __fma_rn(a, b, -r);
 }
 
+// Tests on the bit pattern (integer pipe), keeping the scarce FP64 pipe for
+// the arithmetic of the error-free transformations.
+__device__ __forceinline__ bool is_zero_bits(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull; }
+__device__ __forceinline__ bool is_finite_bits(double x) {
+  return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffull) != 0x7ffull;
+}
+
 // Alg. 4 with the early exit of Sec. 4.2; returns the value carried out of
 // the last of the p terms (0 when nothing was lost).
 __device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, double x) {
@@ -283,7 +290,7 @@ __device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, do
       two_sum(f[i], x, r, s);
       f[i] = r;
       x = s;
-      if (x == 0.0) break;
+      if (is_zero_bits(x)) break;
     }
   }
   return x;
@@ -294,7 +301,7 @@ __device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[
   bool lost = false;
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) {
-    if (i < p && b[i] != 0.0) lost |= fpe_accumulate(a, p, b[i]) != 0.0;
+    if (i < p && !is_zero_bits(b[i])) lost |= !is_zero_bits(fpe_accumulate(a, p, b[i]));
   }
   return lost;
 }
@@ -304,12 +311,14 @@ constexpr double kTwoProdSafe = 0x1p-969;  // |a*b| >= this: twoprod's error ter
 // One element of the FPE dot: product into the result expansion, its error
 // into the error expansion.  Returns true if bits may have been lost.
 __device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&err)[kFpeMax], int p, double a, double b) {
+  if (is_zero_bits(a) || is_zero_bits(b)) return false;  // adds nothing
   double r, s;
   two_prod(a, b, r, s);
-  bool lost = (a != 0.0) & (b != 0.0) & (fabs(r) < kTwoProdSafe);
-  lost |= !isfinite(r);
-  lost |= fpe_accumulate(res, p, r) != 0.0;
-  if (s != 0.0) lost |= fpe_accumulate(err, p, s) != 0.0;
+  // |r| < 2^-969 (exponent field below 54) or r not finite: bits may be lost
+  const unsigned rexp = (unsigned)(((unsigned long long)__double_as_longlong(r) >> 52) & 0x7ffull);
+  bool lost = (rexp < 54u) | (rexp == 0x7ffu);
+  lost |= !is_zero_bits(fpe_accumulate(res, p, r));
+  if (!is_zero_bits(s)) lost |= !is_zero_bits(fpe_accumulate(err, p, s));
   return lost;
 }
 

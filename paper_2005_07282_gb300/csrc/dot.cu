@@ -6,6 +6,7 @@
 
 #include "device.cuh"
 #include "host.h"
+#include "softeft.cuh"
 
 namespace rpcg {
 
@@ -35,7 +36,7 @@ int sm_count() {
 // ------------------------------------------------------------------ scratch
 constexpr int kDotBlock = 256;
 constexpr int kDotMaxGrid = 2048;
-constexpr int kFpeDotMaxGrid = kDotBlock;  // the last CTA merges one expansion per thread
+constexpr int kFpeDotMaxGrid = 640;  // CTA expansions (the scratch must fit the 64 KiB no-allocation array); the last CTA pre-merges them kDotBlock-strided
 
 struct DotScratch {
   // zeroed before every launch (header)
@@ -136,6 +137,36 @@ __device__ void fpe_tree(double* sf, int count, int p, int* lost) {
   __syncthreads();
 }
 
+// Elementwise Alg. 1 (which = 0) or Alg. 2 (which = 1) on the integer pipe;
+// zero, non-finite and out-of-range elements take the FP64 formulas, so
+// every output equals the FP64 algorithm's.
+__global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ r,
+                      double* __restrict__ s, int which) {
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const double x = a[i], y = b[i];
+    double rr = 0.0, ss = 0.0;
+    bool hw = !isfinite(x) || !isfinite(y) || x == 0.0 || y == 0.0;
+    if (!hw) {
+      SF R, S;
+      bool bad = false;
+      if (which == 0) sf_twosum(sf_from(x), sf_from(y), R, S, bad);
+      else sf_twoprod(x, y, R, S, bad);
+      if (!bad) {
+        rr = sf_to_double(R);
+        ss = sf_to_double(S);
+      } else {
+        hw = true;
+      }
+    }
+    if (hw) {
+      if (which == 0) two_sum(x, y, rr, ss);
+      else two_prod(x, y, rr, ss);
+    }
+    r[i] = rr;
+    s[i] = ss;
+  }
+}
+
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,
                                                    const double* __restrict__ b, int p, DotScratch* ws, double* out,
@@ -148,11 +179,42 @@ __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __re
   double res[kFpeMax], err[kFpeMax];
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) res[i] = err[i] = 0.0;
-  bool lost = false;
+  bool lost = false, nonfinite = false;
   const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * BLOCK;
-  for (int64_t i = tid; i < n; i += nthr) lost |= fpe_dot_step(res, err, p, __ldcs(a + i), __ldcs(b + i));
+  // the expansion work of one element depends on the previous one, so the
+  // loads run one chunk of U elements ahead of it
+  constexpr int U = 4;
+  double xa[U], ya[U];
+#pragma unroll
+  for (int u = 0; u < U; u++) {
+    const int64_t i = tid + u * nthr;
+    xa[u] = i < n ? __ldcs(a + i) : 0.0;
+    ya[u] = i < n ? __ldcs(b + i) : 0.0;
+  }
+  for (int64_t i0 = tid; i0 < n; i0 += U * nthr) {
+    double xb[U], yb[U];
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      const int64_t i = i0 + (U + u) * nthr;
+      xb[u] = i < n ? __ldcs(a + i) : 0.0;
+      yb[u] = i < n ? __ldcs(b + i) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      if (i0 + u * nthr < n) {
+        if (!is_finite_bits(xa[u]) || !is_finite_bits(ya[u])) nonfinite = true;
+        else lost |= fpe_dot_step(res, err, p, xa[u], ya[u]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) {
+      xa[u] = xb[u];
+      ya[u] = yb[u];
+    }
+  }
   lost |= fpe_sum(res, err, p);
+  if (nonfinite) atomicOr(&ws->flags, 4u);
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) sf[threadIdx.x * kFpeMax + i] = res[i];
   __syncthreads();
@@ -164,15 +226,29 @@ __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __re
   }
   if (is_last_block(&ws->counter)) {
     const int g = gridDim.x;
-    for (int t = threadIdx.x; t < BLOCK; t += BLOCK) {
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = (t < g) ? __ldcg(&ws->fpe[t * kFpeMax + i]) : 0.0;
-    }
     if (threadIdx.x == 0) slost = 0;
-    fpe_tree<BLOCK>(sf, g, p, &slost);
+    __syncthreads();
+    {
+      // thread t merges CTA expansions t, t + BLOCK, t + 2 BLOCK, ... in
+      // that order, then the fixed tree merges the BLOCK partial results
+      const int t = threadIdx.x;
+      double A[kFpeMax], B[kFpeMax];
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) A[i] = t < g ? __ldcg(&ws->fpe[t * kFpeMax + i]) : 0.0;
+      bool l2 = false;
+      for (int c = t + BLOCK; c < g; c += BLOCK) {
+#pragma unroll
+        for (int i = 0; i < kFpeMax; i++) B[i] = __ldcg(&ws->fpe[c * kFpeMax + i]);
+        l2 |= fpe_sum(A, B, p);
+      }
+#pragma unroll
+      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = A[i];
+      if (l2) atomicOr(&slost, 1);
+    }
+    fpe_tree<BLOCK>(sf, g < BLOCK ? g : BLOCK, p, &slost);
     if (threadIdx.x == 0) {
       const unsigned int f = atomicExch(&ws->flags, 0u);
-      bool fin = true;
+      bool fin = !(f & 4u);
       for (int i = 0; i < p; i++) fin &= isfinite(sf[i]);
       const bool ok = fin && !(f & 2u) && !slost;
       *out = fin ? exact_sum_terms(sf, p, sdig, sD) : __longlong_as_double(0x7FF8000000000000ll);
@@ -251,7 +327,7 @@ static rpcg_status dot_common(int kind, int64_t n, const double* a, const double
     if (kind == 0) {
       k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
     } else if (kind == 1) {
-      k_dot_fpe<kDotBlock><<<dot_grid(n, 4, kFpeDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
+      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kFpeDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
     } else {
       k_dot_plain<kDotBlock><<<dot_grid(n, 4, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
     }
@@ -276,6 +352,27 @@ rpcg_status rpcg_dot_fpe(int64_t n, const double* a, const double* b, int32_t p,
 
 rpcg_status rpcg_dot_plain(int64_t n, const double* a, const double* b, double* out, void* stream) {
   return dot_common(2, n, a, b, 0, out, nullptr, stream);
+}
+
+static rpcg_status eft_common(int which, int64_t n, const double* a, const double* b, double* r, double* s,
+                              void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(n >= 0, "n must be >= 0");
+  RPCG_CHECK_ARG(n == 0 || (a && b && r && s), "NULL array");
+  if (n == 0) return RPCG_OK;
+  int64_t g = (n + 255) / 256;
+  if (g > sm_count() * 8) g = sm_count() * 8;
+  k_eft<<<(int)g, 256, 0, (cudaStream_t)stream>>>(n, a, b, r, s, which);
+  RPCG_CUDA_TRY(cudaGetLastError());
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_eft_twosum(int64_t n, const double* a, const double* b, double* r, double* s, void* stream) {
+  return eft_common(0, n, a, b, r, s, stream);
+}
+
+rpcg_status rpcg_eft_twoprod(int64_t n, const double* a, const double* b, double* r, double* s, void* stream) {
+  return eft_common(1, n, a, b, r, s, stream);
 }
 
 }  // extern "C"

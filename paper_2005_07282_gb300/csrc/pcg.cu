@@ -107,7 +107,8 @@ __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long*
     R.bad |= e.bad;
     exact_deposit(R.win[j], sacc + j * kNDig * kCopies, threadIdx.x & (kCopies - 1), e);
   } else if constexpr (V == RPCG_FPE) {
-    R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b);
+    if (!is_finite_bits(a) || !is_finite_bits(b)) R.bad = true;
+    else R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b);
   } else {
     R.acc[j] = __fma_rn(a, b, R.acc[j]);
   }
@@ -147,6 +148,7 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
 #pragma unroll
     for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, ws->digits[j]);
   } else if constexpr (V == RPCG_FPE) {
+    if (R.bad) atomicOr(&ws->flags, 1u);
     for (int j = 0; j < NACC; j++) {
       R.lost[j] |= fpe_sum(R.res[j], R.err[j], p);
       __syncthreads();
@@ -210,7 +212,13 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
     }
     if (threadIdx.x == 0) {
       const unsigned int f = atomicExch(&ws->flags, 0u);
-      for (int j = 0; j < NACC; j++) fs->lost[j] |= (f & (2u << j)) ? 1 : 0;
+      for (int j = 0; j < NACC; j++) {
+        fs->lost[j] |= (f & (2u << j)) ? 1 : 0;
+        if (f & 1u) {  // a non-finite operand
+          fs->lost[j] = 1;
+          fs->value[j] = __longlong_as_double(0x7FF8000000000000ll);
+        }
+      }
     }
   } else {
     for (int j = 0; j < NACC; j++) {
