@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--side", type=int, default=256, help="grid side of the Poisson workload")
     ap.add_argument("--stencil", type=int, choices=[7, 27], default=27, help="7- or 27-point Poisson")
+    ap.add_argument("--variant", choices=["exblas", "fpe", "plain"], default="exblas",
+                    help="dot variant of the timed solves (the headline uses exblas)")
     ap.add_argument("--band", type=int, default=0, metavar="BW",
                     help="use the band matrix of half-bandwidth BW (the paper's performance workload) instead")
     ap.add_argument("--band-n", type=int, default=4_000_000, help="rows of the band matrix")
@@ -250,7 +252,7 @@ def gpu_arm(args, rank, world, local_rank):
 
     # ---- warm-up (builds and caches the graphs)
     for _ in range(args.warmup):
-        r = solve("exblas")
+        r = solve(args.variant)
     iters_per_solve = r["iterations"]
     status = r["status"]
 
@@ -262,7 +264,7 @@ def gpu_arm(args, rank, world, local_rank):
     e0.record(stream)
     total_iters = 0
     for _ in range(args.steps):
-        r = solve("exblas")
+        r = solve(args.variant)
         total_iters += r["iterations"]
     e1.record(stream)
     barrier()
@@ -303,6 +305,15 @@ def gpu_arm(args, rank, world, local_rank):
         torch.cuda.synchronize()
         extras["fpe_iters_per_s"] = rf["iterations"] / (e0.elapsed_time(e1) / 1e3)
         extras["fpe_sample_iterations"] = rf["iterations"]
+        # the paper's Poisson sweet spot (FPE3) and the adaptive size
+        for label, fs in (("fpe3", 3), ("fpe_adaptive", 0)):
+            e0.record(stream)
+            rr = solve("fpe", max_iter=fit, fpe_size=fs)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            extras[f"{label}_iters_per_s"] = rr["iterations"] / (e0.elapsed_time(e1) / 1e3)
+            extras[f"{label}_inexact_dots"] = rr["fpe_inexact_count"]
+            extras[f"{label}_size_used"] = rr["fpe_size_used"]
         # per-pass event timing (same kernels launched one by one), bounded iterations
         x.zero_()
         prof = M.solve_profiled(d_b, x, variant="exblas", tol=args.tol, max_iter=min(60, iters_per_solve))
@@ -320,6 +331,10 @@ def gpu_arm(args, rank, world, local_rank):
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": pass_a_bytes(n, nnz), "avg_launch_ms": a_ms}
         extras["pass_ms"] = {"A": a_ms, "B": b_ms, "C": c_ms}
+        x.zero_()
+        pf = M.solve_profiled(d_b, x, variant="fpe", tol=args.tol, max_iter=min(30, iters_per_solve))
+        lf = max(pf["launches"]["A"], 1)
+        extras["pass_ms_fpe"] = {k: pf["pass_ms"][k] / lf for k in ("A", "B", "C")}
         it_ms = ms / max(total_iters, 1)
         extras["iteration_roofline"] = {"bytes_per_iter": iter_bytes(n, nnz), "ms_per_iter": it_ms,
                                         "achieved_gbs": iter_bytes(n, nnz) / (it_ms * 1e-3) / 1e9,
@@ -382,7 +397,7 @@ def gpu_arm(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl_name(args) + " exblas", "n": n, "nnz": nnz, "tol": args.tol,
+                "config": {"workload": wl_name(args) + " " + args.variant, "n": n, "nnz": nnz, "tol": args.tol,
                            "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
                            "solve_status": status, "step": "one complete solve from x0 = 0",
                            "l2": "inputs larger than L2 (CSR 5.46 GB streamed every iteration)",
@@ -486,11 +501,16 @@ def batch_arm(args):
     rows = sum(A.n for A in mats)
     nnz = sum(A.nnz for A in mats)
     blk, tile = Bt.tuned()
+    moved = sum(r["iterations"] * iter_bytes(A.n, A.nnz) for r, A in zip(res, mats))
+    peak, peak_kind = hbm_peak()
     print(json.dumps({"workload": f"batch of {args.batch} diffusion7 systems, s~U{{8..64}}, tol 1e-10, exblas",
                       "rows": rows, "nnz": nnz, "solves_per_s": args.batch / (ms / 1e3), "ms_per_batch": ms,
                       "iterations": {"total": sum(its), "min": min(its), "max": max(its),
                                      "mean": sum(its) / len(its)},
                       "system_iters_per_s": sum(its) / (ms / 1e3),
+                      "algorithmic_bytes_per_batch": moved,
+                      "achieved_gbs": moved / (ms * 1e-3) / 1e9,
+                      "roofline_frac": moved / (ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
                       "sequential_solo_ms": solo_ms, "speedup_vs_sequential": solo_ms / ms,
                       "bit_identical_to_solo": bool(same), "statuses": sorted(set(r["status"] for r in res)),
                       "autotuned": {"block": blk, "tile": tile}, "steps": args.steps, "warmup": args.warmup,
@@ -541,10 +561,13 @@ def serve_arm(args):
         t_start = time.perf_counter()
         stop_at = t_start + duration
 
+        moved = [0]
+
         def collect(t, ts_submit, req):
             x, r = srv.wait(t)
             now = time.perf_counter()
             with lock:
+                moved[0] += r["iterations"] * iter_bytes(req[0].n, req[0].nnz)
                 lat.append((now - ts_submit) * 1e6)
                 qs.append(r["queue_us"])
                 ss.append(r["service_us"])
@@ -588,7 +611,9 @@ def serve_arm(args):
         for th in collectors:
             th.join()
         wall = time.perf_counter() - t_start
+        peak, _ = hbm_peak()
         return {"requests": done_count[0], "wall_s": wall, "solves_per_s": done_count[0] / wall,
+                "achieved_gbs": moved[0] / wall / 1e9, "roofline_frac": moved[0] / wall / 1e9 / peak,
                 "latency_us": {"p50": pct(lat, 50), "p99": pct(lat, 99)},
                 "queue_us": {"p50": pct(qs, 50), "p99": pct(qs, 99)},
                 "service_us": {"p50": pct(ss, 50), "p99": pct(ss, 99)},

@@ -67,7 +67,8 @@ typedef struct rpcg_server_s *rpcg_server_t;
 typedef struct {
     double tol;         /* stop when RN(sqrt(tau) / ||b||) < tol (default 1e-8) */
     int32_t max_iter;   /* loop bodies at most (default 1000) */
-    int32_t fpe_size;   /* terms per expansion p, 1..8 (default 8, Sec. 4.2) */
+    int32_t fpe_size;   /* terms per expansion p, 1..8 (default 8, Sec. 4.2); 0 = adaptive: start at 3 (Sec. 4.3's
+                           size for Poisson) and add a term after every dot that lost bits, up to 8 */
     int32_t fpe_strict; /* fpe variant: 0 = recompute an inexact dot exactly (default), 1 = report RPCG_FPE_INEXACT */
     int32_t block;      /* threads per CTA of the streaming passes: 0 = auto, else 128, 256 or 512 */
     int32_t grid;       /* CTAs of the streaming passes: 0 = auto, else 1 .. 4096 */
@@ -82,7 +83,7 @@ typedef struct {
     double relres;             /* RN(sqrt(tau) / ||b||) at the last loop test */
     double tau;                /* <r, r> at the last loop test */
     int32_t fpe_inexact_count; /* fpe variant: dots whose expansion lost bits */
-    int32_t reserved;
+    int32_t fpe_size_used;     /* fpe variant: expansion size at the end (grows when fpe_size = 0) */
 } rpcg_result;
 
 /* Fill `o` with the defaults listed in rpcg_opts. */

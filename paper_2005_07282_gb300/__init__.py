@@ -42,11 +42,11 @@ class Opts(ctypes.Structure):
 
 class Result(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("status", ctypes.c_int32), ("relres", ctypes.c_double),
-                ("tau", ctypes.c_double), ("fpe_inexact_count", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("tau", ctypes.c_double), ("fpe_inexact_count", ctypes.c_int32), ("fpe_size_used", ctypes.c_int32)]
 
     def as_dict(self):
         return dict(iterations=self.iterations, status=self.status, relres=self.relres, tau=self.tau,
-                    fpe_inexact_count=self.fpe_inexact_count)
+                    fpe_inexact_count=self.fpe_inexact_count, fpe_size_used=self.fpe_size_used)
 
 
 class ServerTiming(ctypes.Structure):

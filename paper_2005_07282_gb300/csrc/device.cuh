@@ -267,6 +267,21 @@ __device__ __forceinline__ void two_sum(double a, double b, double& r, double& s
   s = __dadd_rn(__dsub_rn(a, __dsub_rn(r, z)), __dsub_rn(b, z));
 }
 
+// Alg. 1's result with half the FP64 work: order the operands by magnitude
+// with an integer compare of their bit patterns, then Dekker's Fast2Sum
+// (r = RN(a + b), z = RN(r - a), s = RN(b - z) is exact when |a| >= |b|).
+// The pair (r, s) of an error-free addition is unique, so this gives the
+// same values as Alg. 1.
+__device__ __forceinline__ void two_sum_ordered(double a, double b, double& r, double& s) {
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFull;
+  const bool sw = ub > ua;
+  const double big = sw ? b : a, small = sw ? a : b;
+  r = __dadd_rn(big, small);
+  const double z = __dsub_rn(r, big);
+  s = __dsub_rn(small, z);
+}
+
 // Alg. 2
 __device__ __forceinline__ void two_prod(double a, double b, double& r, double& s) {
   r = __dmul_rn(a, b);
@@ -287,7 +302,7 @@ __device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, do
   for (int i = 0; i < kFpeMax; i++) {
     if (i < p) {
       double r, s;
-      two_sum(f[i], x, r, s);
+      two_sum_ordered(f[i], x, r, s);
       f[i] = r;
       x = s;
       if (is_zero_bits(x)) break;

@@ -149,6 +149,7 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
     for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, ws->digits[j]);
   } else if constexpr (V == RPCG_FPE) {
     if (R.bad) atomicOr(&ws->flags, 1u);
+#pragma unroll  // constant indices keep the expansions in registers
     for (int j = 0; j < NACC; j++) {
       R.lost[j] |= fpe_sum(R.res[j], R.err[j], p);
       __syncthreads();
@@ -164,6 +165,7 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
       }
     }
   } else {
+#pragma unroll
     for (int j = 0; j < NACC; j++) {
       const double s = block_sum_fixed<BLOCK>(R.acc[j], fs->sw);
       if (threadIdx.x == 0) ws->partials[j][blockIdx.x] = s;
@@ -290,7 +292,7 @@ __device__ void finalize_b(double beta, double tau, SolveState* st, const SolveA
 
 // ------------------------------------------------------------------ kernels
 
-__global__ void k_init_state(SolveState* st, int n) {
+__global__ void k_init_state(SolveState* st, const SolveArgs* args) {
   st->rho = st->beta = st->beta_old = st->gamma = st->bnorm = 0.0;
   st->tau = st->rel = __longlong_as_double(0x7FF8000000000000ll);
   st->iter = 0;
@@ -300,6 +302,14 @@ __global__ void k_init_state(SolveState* st, int n) {
   st->redo = 0;
   st->fpe_inexact = 0;
   st->active = 0;
+  // adaptive expansion size starts at 3, the size Sec. 4.3 finds enough for Poisson
+  st->fpe_p = args->fpe_size > 0 ? args->fpe_size : 3;
+}
+
+// Adaptive expansion size (fpe_size = 0): after a dot that lost bits, the
+// following dots use one more term (up to 8).
+__device__ __forceinline__ void fpe_grow(SolveState* st, const SolveArgs* args) {
+  if (args->fpe_size == 0 && st->fpe_p < kFpeMax) st->fpe_p += 1;
 }
 
 // Jacobi preconditioner (Sec. 3.1, Sec. 4.3): inv_i = RN(1 / a_ii).  Rows
@@ -342,7 +352,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_a(MatDev m, const double* __rest
     if (blockIdx.x == 0 && threadIdx.x == 0) stop_loop(st, args, cond);
     return;
   }
-  const int p = args->fpe_size;
+  const int p = st->fpe_p;
   if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc);
   __syncthreads();
   Reducer<V, 1> R;
@@ -359,6 +369,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_a(MatDev m, const double* __rest
     }
     if (V == RPCG_FPE && fs->lost[0]) {
       st->fpe_inexact += 1;
+      fpe_grow(st, args);
       if (!args->fpe_strict) {
         st->redo = 1;  // recompute this dot exactly (k_redo_a)
         return;
@@ -381,7 +392,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
     if (st->status != 0 && blockIdx.x == 0 && threadIdx.x == 0) stop_loop(st, args, cond);
     return;
   }
-  const int p = args->fpe_size;
+  const int p = st->fpe_p;
   double* __restrict__ x = args->x;
   const double rho = st->rho, nrho = -st->rho;
   if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc, 2);
@@ -401,6 +412,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
   if (red_finish<V, 2, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     if (V == RPCG_FPE && (fs->lost[0] || fs->lost[1])) {
       st->fpe_inexact += (fs->lost[0] ? 1 : 0) + (fs->lost[1] ? 1 : 0);
+      fpe_grow(st, args);
       if (!args->fpe_strict) {
         st->redo = 2;  // recompute both dots exactly (k_redo_b)
         return;
@@ -637,7 +649,7 @@ static rpcg_status build_graph(rpcg_matrix_t A, int grid, cudaGraph_t* out_graph
 
   cudaGraphNode_t n_init, n_inv, n_spmv, n_setup, n_loop;
   {
-    void* a[] = {&st, &n};
+    void* a[] = {&st, &args};
     RPCG_CUDA_TRY(add_kernel(g, &n_init, nullptr, 0, (const void*)k_init_state, 1, 1, 0, a));
   }
   {
@@ -755,7 +767,7 @@ static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaSt
   };
   cudaError_t e;
   e = cudaEventRecord(ev[0], s);
-  k_init_state<<<1, 1, 0, s>>>(st, n);
+  k_init_state<<<1, 1, 0, s>>>(st, args);
   k_inv_diag<<<c.grid_small, BLOCK, 0, s>>>(m, inv, st);
   k_spmv<BLOCK><<<c.grid_tiles, BLOCK, c.smem_spmv, s>>>(m, x0, w);
   k_setup<V, BLOCK><<<c.grid_stream, BLOCK, c.smem_s, s>>>(m, w, inv, r, d, ws, st, args, cond);
@@ -1070,7 +1082,7 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
   RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS || v == RPCG_FPE, "unknown variant");
   RPCG_CHECK_ARG(opt.max_iter >= 0, "max_iter must be >= 0");
   RPCG_CHECK_ARG(!(opt.tol < 0.0) && !std::isnan(opt.tol), "tol must be >= 0");
-  RPCG_CHECK_ARG(opt.fpe_size >= 1 && opt.fpe_size <= kFpeMax, "fpe_size must be 1..8");
+  RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.grid >= 0 && opt.grid <= kMaxPassGrid, "grid must be 0..4096");
   const int block = pick_block(opt.block);
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == block, "block must be 0, 128, 256 or 512");
@@ -1136,7 +1148,7 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
   res->relres = hs.rel;
   res->tau = hs.tau;
   res->fpe_inexact_count = hs.fpe_inexact;
-  res->reserved = 0;
+  res->fpe_size_used = v == RPCG_FPE ? hs.fpe_p : 0;
   return (rpcg_status)status;
 }
 

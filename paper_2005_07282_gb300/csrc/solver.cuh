@@ -30,7 +30,7 @@ struct SolveArgs {
 // Solver state, device resident.
 struct SolveState {
   double rho, beta, beta_old, tau, gamma, bnorm, rel;
-  int iter, status, bad_row, bzero, redo, fpe_inexact, active, pad;
+  int iter, status, bad_row, bzero, redo, fpe_inexact, active, fpe_p;  // fpe_p: expansion size in use
 };
 
 // Device matrix.  The handle stores A in SELL-32 form: rows are grouped

@@ -236,3 +236,25 @@ def test_band_matrix_spmv_and_pcg(rpcg, cuda, oracle_lib):
     r = M.solve(_dev(b, cuda), xd, tol=1e-8, max_iter=500)
     assert r["iterations"] == ref["iterations"] and r["status"] == 0
     assert np.array_equal(bits(xd.cpu().numpy()), bits(ref["x"]))
+
+
+def test_pcg_fpe_adaptive_size(rpcg, cuda, oracle_lib):
+    """fpe_size = 0 starts at 3 terms and grows after dots that lose bits;
+    the trajectory stays the exact one."""
+    import torch
+    A = synth.diffusion7(9, SEED + 7)[0]
+    b = _dev(_rhs(oracle_lib, A, SEED + 8), cuda)
+    M = rpcg.Matrix.from_csr(A)
+    xe = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    re = M.solve(b, xe, variant="exblas", tol=1e-10, max_iter=2000)
+    xa = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    ra = M.solve(b, xa, variant="fpe", tol=1e-10, max_iter=2000, fpe_size=0)
+    assert ra["iterations"] == re["iterations"]
+    assert torch.equal(xa.view(torch.int64), xe.view(torch.int64))
+    if ra["fpe_inexact_count"] == 0:
+        assert ra["fpe_size_used"] == 3
+    else:  # each finalisation that saw a lost dot adds one term
+        assert 3 < ra["fpe_size_used"] <= min(8, 3 + ra["fpe_inexact_count"])
+    x1 = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    r1 = M.solve(b, x1, variant="fpe", tol=1e-10, max_iter=2000, fpe_size=1)
+    assert r1["fpe_size_used"] == 1 and r1["fpe_inexact_count"] > 0
