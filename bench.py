@@ -469,10 +469,14 @@ def batch_arm(args):
     xs = [torch.zeros(A.n, dtype=torch.float64, device=dev) for A in mats]
     opts = dict(tol=1e-10, max_iter=args.max_iter)
     Bt = P.Batch(Ms)
+    if args.eager:
+        Bt.solve(bs, xs, variant="exblas", **opts)  # autotune once (graph form), then time pass by pass
 
     def run():
         for x in xs:
             x.zero_()
+        if args.eager:  # kernel by kernel (profilers see every launch)
+            return Bt.solve_profiled(bs, xs, variant="exblas", **opts)[0]
         return Bt.solve(bs, xs, variant="exblas", **opts)
 
     for _ in range(args.warmup):
@@ -501,19 +505,27 @@ def batch_arm(args):
     rows = sum(A.n for A in mats)
     nnz = sum(A.nnz for A in mats)
     blk, tile = Bt.tuned()
+    for x in xs:
+        x.zero_()
+    _, pass_ms, pass_launches = Bt.solve_profiled(bs, xs, variant="exblas", **opts)
     moved = sum(r["iterations"] * iter_bytes(A.n, A.nnz) for r, A in zip(res, mats))
+    # rows still iterating at every 40th iteration (the shrinking active set)
+    active_rows = {k: sum(A.n for r, A in zip(res, mats) if r["iterations"] > k) for k in range(0, max(its), 40)}
     peak, peak_kind = hbm_peak()
     print(json.dumps({"workload": f"batch of {args.batch} diffusion7 systems, s~U{{8..64}}, tol 1e-10, exblas",
                       "rows": rows, "nnz": nnz, "solves_per_s": args.batch / (ms / 1e3), "ms_per_batch": ms,
                       "iterations": {"total": sum(its), "min": min(its), "max": max(its),
                                      "mean": sum(its) / len(its)},
                       "system_iters_per_s": sum(its) / (ms / 1e3),
-                      "algorithmic_bytes_per_batch": moved,
+                      "algorithmic_bytes_per_batch": moved, "active_rows_by_iteration": active_rows,
                       "achieved_gbs": moved / (ms * 1e-3) / 1e9,
                       "roofline_frac": moved / (ms * 1e-3) / 1e9 / peak, "peak_kind": peak_kind,
                       "sequential_solo_ms": solo_ms, "speedup_vs_sequential": solo_ms / ms,
                       "bit_identical_to_solo": bool(same), "statuses": sorted(set(r["status"] for r in res)),
-                      "autotuned": {"block": blk, "tile": tile}, "steps": args.steps, "warmup": args.warmup,
+                      "autotuned": {"block": blk, "tile": tile},
+                      "pass_ms_eager": {k: round(v, 3) for k, v in pass_ms.items()},
+                      "pass_launches_eager": pass_launches, "timed_eager": bool(args.eager),
+                      "steps": args.steps, "warmup": args.warmup,
                       "generation_s": gen_s}), flush=True)
 
 

@@ -249,9 +249,10 @@ rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double *b_host, double *x_hos
  *
  * rpcg_batch_solve -- Jacobi-PCG (the steps of rpcg_solve, Fig. 1/Fig. 2)
  * on every system of the batch in one launch sequence: each pass is one
- * persistent kernel over work units of at most o->tile rows of one system;
- * each system has its own exact accumulators, scalars and convergence test
- * and leaves the work when it stops.
+ * persistent kernel whose CTAs take work units (o->tile rows of one system)
+ * of the systems still iterating from a shared counter; each system has its
+ * own exact accumulators, scalars and convergence test and leaves the work
+ * when it stops.
  *   b, x      host arrays of `count` device pointers (b[i], x[i]: n_i doubles;
  *             x[i] in = x0, out = the iterate).
  *   v         RPCG_EXBLAS (bit-identical to rpcg_solve of each system alone)
@@ -260,7 +261,8 @@ rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double *b_host, double *x_hos
  *             count x (max_iter + 1) doubles (row i for system i).
  *             o->block (0, 128, 256) and o->tile (0 or rows per unit): a zero
  *             picks them with the autotuner on the first solve of the batch
- *             (short timed runs of each candidate on internal buffers; the
+ *             (block 128 or 256 x tile 1024, 4096 or 16384 rows;
+ *             short timed runs of each candidate on internal buffers; the
  *             choice is kept for later solves).
  *   res       host array of `count` results.
  * Returns the worst status over the systems.  Synchronises the stream.
@@ -269,6 +271,21 @@ rpcg_status rpcg_batch_create(rpcg_batch_t *B, int32_t count, const rpcg_matrix_
 rpcg_status rpcg_batch_destroy(rpcg_batch_t B);
 rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double *const *b, double *const *x, int32_t v, const rpcg_opts *o,
                              rpcg_result *res, void *stream);
+/*
+ * rpcg_batch_solve_profiled -- rpcg_batch_solve with the batch kernels
+ * launched one by one from the host and CUDA events recorded on `stream`
+ * around each kind of pass; bit-identical results.  A zero o->block or
+ * o->tile takes the autotuned value if there is one (else 128 and 4096 rows);
+ * the autotuner is not run.
+ *   pass_ms   host array of 5 floats: total milliseconds of the set-up
+ *             (state reset, inverse diagonal, set-up pass), pass A, pass B,
+ *             pass C and the retire/list kernel.
+ *   launches  optional host array of 5 int32: launches of each.
+ * It synchronises the stream once per pass: a measurement tool.
+ */
+rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double *const *b, double *const *x, int32_t v,
+                                      const rpcg_opts *o, rpcg_result *res, float *pass_ms, int32_t *launches,
+                                      void *stream);
 /* Block size and tile the autotuner picked (0, 0 before the first autotuned solve). */
 rpcg_status rpcg_batch_tuned(rpcg_batch_t B, int32_t *block, int32_t *tile);
 

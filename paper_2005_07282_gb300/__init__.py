@@ -28,7 +28,7 @@ EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
     "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
-    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
+    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_solve_profiled", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
     "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_eft_twosum",
     "rpcg_eft_twoprod",
 ]
@@ -306,6 +306,24 @@ class Batch:
         if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
             _check(st, "rpcg_batch_solve")
         return [r.as_dict() for r in res]
+
+    def solve_profiled(self, bs, xs, variant="exblas", stream=None, **opts):
+        """solve() launched pass by pass with events; returns (results,
+        {pass: ms}, {pass: launches})."""
+        n = len(self.mats)
+        assert len(bs) == n and len(xs) == n
+        barr = (ctypes.c_void_p * n)(*[_dptr(t).value for t in bs])
+        xarr = (ctypes.c_void_p * n)(*[_dptr(t).value for t in xs])
+        res = (Result * n)()
+        ms = (ctypes.c_float * 5)()
+        nl = (ctypes.c_int32 * 5)()
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o = make_opts(**opts)
+        st = lib().rpcg_batch_solve_profiled(self._h, barr, xarr, v, ctypes.byref(o), res, ms, nl, _stream(stream))
+        if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
+            _check(st, "rpcg_batch_solve_profiled")
+        names = ("setup", "A", "B", "C", "list")
+        return [r.as_dict() for r in res], dict(zip(names, list(ms))), dict(zip(names, list(nl)))
 
     def tuned(self):
         b, t = ctypes.c_int32(), ctypes.c_int32()

@@ -1,15 +1,17 @@
 // Batched Jacobi-PCG: many independent SPD systems in one launch sequence.
 //
 // The systems keep their own matrix handles (SELL-32 copy, r, d, w, inv);
-// the batch adds per-system scalars, per-system long accumulators and a list
-// of work units -- ranges of at most `tile` rows of one system.  Each pass
-// (set-up, A, B, C of Fig. 2) is one persistent kernel over all units of the
-// systems still iterating; every unit deposits its dot products into its
-// system's accumulators, and the CTA that completes a system's last unit
-// finishes that system's reduction and scalar step (rho, or beta, tau,
-// gamma, relres and its own convergence test).  Systems that have converged
-// drop out of later passes.  A one-thread kernel sets the while node's
-// condition from the count of systems still active.
+// the batch adds per-system scalars and per-system long accumulators, and
+// cuts every system into work units of `tile` rows.  Each pass (set-up, A,
+// B, C of Fig. 2) is one persistent kernel over the units of the systems
+// still iterating, which CTAs take in chunks from a work counter; every unit
+// deposits its dot products into its system's accumulators, and the CTA that
+// completes a system's last unit finishes that system's reduction and
+// scalar step (rho, or beta, tau, gamma, relres and its own convergence
+// test).  After every iteration a one-block kernel retires the systems that
+// stopped, lists the units of the others for the next iteration and sets
+// the while node's condition, so converged systems cost nothing afterwards
+// and the last few systems still iterating are spread over all SMs.
 //
 // Every row, element and scalar operation is the one rpcg_solve performs
 // and exact dots do not depend on how the work is split, so each system's
@@ -30,21 +32,20 @@
 
 struct rpcg_batch_s {
   int count = 0;
-  int nactive0 = 0;  // systems with at least one row
   std::vector<rpcg_matrix_t> mats;
   rpcg::SysDev* d_sys = nullptr;
   rpcg::SysDev* h_sys = nullptr;  // pinned
   rpcg::SysState* d_state = nullptr;
   rpcg::SysState* h_state = nullptr;  // pinned
   rpcg::SysRed* d_red = nullptr;
-  rpcg::BatchScratchHead* d_head = nullptr;
-  // per tile size: units, unit counts, partials
+  rpcg::BatchHead* d_head = nullptr;
+  int* d_aprefix = nullptr;  // [count + 1] listed units, rebuilt by the kernels
+  // per tile size: units per system, their prefix, plain partials
   struct Layout {
-    rpcg::Unit* units = nullptr;
-    int* unit_count = nullptr;
+    int* nunits = nullptr;   // [count]
+    int* uprefix = nullptr;  // [count + 1]
     double* partials = nullptr;
-    int* d_nunits = nullptr;  // the unit count, read by the kernels
-    int nunits = 0;
+    int total = 0;  // units of all systems
   };
   std::map<int, Layout> layouts;
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (variant, block, tile)
@@ -60,25 +61,19 @@ static rpcg_status batch_layout(rpcg_batch_t B, int tile, rpcg_batch_s::Layout**
     *out = &it->second;
     return RPCG_OK;
   }
-  std::vector<Unit> units;
-  std::vector<int> counts(B->count, 0);
+  std::vector<int> counts(B->count, 0), prefix(B->count + 1, 0);
   for (int s = 0; s < B->count; s++) {
     const int n = B->mats[s]->m.n;
-    for (int r0 = 0; r0 < n; r0 += tile) {
-      units.push_back(Unit{s, r0, std::min(n, r0 + tile)});
-      counts[s]++;
-    }
-    if (n == 0) counts[s] = 0;
+    counts[s] = (int)(((long long)n + tile - 1) / tile);
+    prefix[s + 1] = prefix[s] + counts[s];
   }
   rpcg_batch_s::Layout L;
-  L.nunits = (int)units.size();
-  RPCG_CUDA_TRY(cudaMalloc(&L.units, std::max<size_t>(1, units.size()) * sizeof(Unit)));
-  RPCG_CUDA_TRY(cudaMalloc(&L.unit_count, std::max<size_t>(1, counts.size()) * sizeof(int)));
-  RPCG_CUDA_TRY(cudaMalloc(&L.partials, std::max<size_t>(1, units.size()) * 3 * sizeof(double)));
-  RPCG_CUDA_TRY(cudaMalloc(&L.d_nunits, sizeof(int)));
-  RPCG_CUDA_TRY(cudaMemcpy(L.d_nunits, &L.nunits, sizeof(int), cudaMemcpyHostToDevice));
-  if (!units.empty()) RPCG_CUDA_TRY(cudaMemcpy(L.units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice));
-  RPCG_CUDA_TRY(cudaMemcpy(L.unit_count, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice));
+  L.total = prefix[B->count];
+  RPCG_CUDA_TRY(cudaMalloc(&L.nunits, counts.size() * sizeof(int)));
+  RPCG_CUDA_TRY(cudaMalloc(&L.uprefix, prefix.size() * sizeof(int)));
+  RPCG_CUDA_TRY(cudaMalloc(&L.partials, std::max<size_t>(1, (size_t)L.total) * 3 * sizeof(double)));
+  RPCG_CUDA_TRY(cudaMemcpy(L.nunits, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice));
+  RPCG_CUDA_TRY(cudaMemcpy(L.uprefix, prefix.data(), prefix.size() * sizeof(int), cudaMemcpyHostToDevice));
   B->layouts[tile] = L;
   *out = &B->layouts[tile];
   return RPCG_OK;
@@ -95,57 +90,67 @@ static cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t* node, const cudaGrap
   return cudaGraphAddKernelNode(node, g, deps, ndeps, &p);
 }
 
+// Grid sizes and dynamic shared memory of the batch kernels for one
+// (variant, block, tile): persistent grids of the occupancy limit.
+struct BatchPlan {
+  int g_setup, g_a, g_b, g_c, g_q;
+  size_t sm1, sm2, sm3;
+};
+
+template <int V, int BLOCK>
+static rpcg_status batch_plan(rpcg_batch_t B, const rpcg_batch_s::Layout* L, BatchPlan* P) {
+  const int count = B->count;
+  P->sm1 = b_smem<V>(1, count);
+  P->sm2 = b_smem<V>(2, count);
+  P->sm3 = b_smem<V>(3, count);
+  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_setup<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm3));
+  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_a<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm1));
+  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm2));
+  auto occ_grid = [&](const void* f, size_t smem) {
+    int occ = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, BLOCK, smem) != cudaSuccess || occ < 1) occ = 1;
+    int g = sm_count() * occ;
+    if (g > L->total) g = L->total > 0 ? L->total : 1;
+    return g;
+  };
+  P->g_setup = occ_grid((const void*)k_b_setup<V, BLOCK>, P->sm3);
+  P->g_a = occ_grid((const void*)k_b_pass_a<V, BLOCK>, P->sm1);
+  P->g_b = occ_grid((const void*)k_b_pass_b<V, BLOCK>, P->sm2);
+  P->g_c = occ_grid((const void*)k_b_pass_c<BLOCK>, 0);
+  P->g_q = occ_grid((const void*)k_b_inv_q, 0);
+  return RPCG_OK;
+}
+
 template <int V, int BLOCK>
 static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cudaGraphExec_t* out_e) {
   rpcg_batch_s::Layout* L = nullptr;
   rpcg_status st = batch_layout(B, tile, &L);
   if (st != RPCG_OK) return st;
-  const size_t sm1 = b_smem<V>(1), sm2 = b_smem<V>(2), sm3 = b_smem<V>(3);
-  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_setup<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3));
-  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_a<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1));
-  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2));
-  auto occ_grid = [&](const void* f, size_t smem) {
-    int occ = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, BLOCK, smem) != cudaSuccess || occ < 1) occ = 1;
-    int g = sm_count() * occ;
-    if (g > L->nunits) g = L->nunits > 0 ? L->nunits : 1;
-    return g;
-  };
-  const int g_setup = occ_grid((const void*)k_b_setup<V, BLOCK>, sm3);
-  const int g_a = occ_grid((const void*)k_b_pass_a<V, BLOCK>, sm1);
-  const int g_b = occ_grid((const void*)k_b_pass_b<V, BLOCK>, sm2);
-  const int g_c = occ_grid((const void*)k_b_pass_c<BLOCK>, 0);
-  const int g_q = occ_grid((const void*)k_b_inv_q, 0);
+  BatchPlan P;
+  st = batch_plan<V, BLOCK>(B, L, &P);
+  if (st != RPCG_OK) return st;
+  const int count = B->count;
+  const int g_setup = P.g_setup, g_a = P.g_a, g_b = P.g_b, g_c = P.g_c, g_q = P.g_q;
+  const size_t sm1 = P.sm1, sm2 = P.sm2, sm3 = P.sm3;
 
   cudaGraph_t g = nullptr;
   RPCG_CUDA_TRY(cudaGraphCreate(&g, 0));
   cudaGraphConditionalHandle cond;
   RPCG_CUDA_TRY(cudaGraphConditionalHandleCreate(&cond, g, 0, 0));
-  SysDev* sys = B->d_sys;
-  SysState* sst = B->d_state;
-  SysRed* red = B->d_red;
-  BatchScratchHead* head = B->d_head;
-  Unit* units = L->units;
-  int* nunits = L->d_nunits;
-  int* ucount = L->unit_count;
-  double* partials = L->partials;
-  int count = B->count;
-  int nactive = B->nactive0;
+  BatchDesc D{B->d_sys, B->d_state, B->d_red, B->d_head, B->d_aprefix, L->nunits, L->uprefix, L->partials, count, tile};
+  int* aprefix = B->d_aprefix;
   cudaGraphNode_t n_init, n_q, n_setup, n_c0, n_loop;
   {
-    void* a[] = {&sys, &sst, &head, &count, &nactive};
-    RPCG_CUDA_TRY(add_node(g, &n_init, nullptr, 0, (const void*)k_b_init, (count + 255) / 256, 256, 0, a));
+    void* a[] = {&D};
+    RPCG_CUDA_TRY(add_node(g, &n_init, nullptr, 0, (const void*)k_b_init, 1, 256, 0, a));
   }
   {
-    void* a[] = {&sys, &units, &nunits, &sst};
+    void* a[] = {&D, &aprefix};
     RPCG_CUDA_TRY(add_node(g, &n_q, &n_init, 1, (const void*)k_b_inv_q, g_q, BLOCK, 0, a));
-  }
-  {
-    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head};
     RPCG_CUDA_TRY(add_node(g, &n_setup, &n_q, 1, (const void*)k_b_setup<V, BLOCK>, g_setup, BLOCK, sm3, a));
   }
   {
-    void* a[] = {&sst, &count, &head, &cond};
+    void* a[] = {&D, &cond};
     RPCG_CUDA_TRY(add_node(g, &n_c0, &n_setup, 1, (const void*)k_b_cond, 1, 256, 0, a));
   }
   cudaGraphNodeParams cp{};
@@ -157,19 +162,13 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaGraphNode_t b_a, b_b, b_c, b_cond;
   {
-    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head};
+    void* a[] = {&D};
     RPCG_CUDA_TRY(add_node(body, &b_a, nullptr, 0, (const void*)k_b_pass_a<V, BLOCK>, g_a, BLOCK, sm1, a));
-  }
-  {
-    void* a[] = {&sys, &units, &nunits, &ucount, &sst, &red, &partials, &head};
     RPCG_CUDA_TRY(add_node(body, &b_b, &b_a, 1, (const void*)k_b_pass_b<V, BLOCK>, g_b, BLOCK, sm2, a));
-  }
-  {
-    void* a[] = {&sys, &units, &nunits, &sst};
     RPCG_CUDA_TRY(add_node(body, &b_c, &b_b, 1, (const void*)k_b_pass_c<BLOCK>, g_c, BLOCK, 0, a));
   }
   {
-    void* a[] = {&sst, &count, &head, &cond};
+    void* a[] = {&D, &cond};
     RPCG_CUDA_TRY(add_node(body, &b_cond, &b_c, 1, (const void*)k_b_cond, 1, 256, 0, a));
   }
   cudaGraphExec_t e = nullptr;
@@ -206,11 +205,11 @@ static void batch_free(rpcg_batch_t B) {
   for (auto& kv : B->graphs) cudaGraphExecDestroy(kv.second);
   for (auto& kv : B->graph_defs) cudaGraphDestroy(kv.second);
   for (auto& kv : B->layouts) {
-    cudaFree(kv.second.units);
-    cudaFree(kv.second.unit_count);
+    cudaFree(kv.second.nunits);
+    cudaFree(kv.second.uprefix);
     cudaFree(kv.second.partials);
-    cudaFree(kv.second.d_nunits);
   }
+  cudaFree(B->d_aprefix);
   cudaFree(B->d_sys);
   cudaFree(B->d_state);
   cudaFree(B->d_red);
@@ -220,20 +219,106 @@ static void batch_free(rpcg_batch_t B) {
   delete B;
 }
 
+static void batch_upload(rpcg_batch_t B, const double* const* b, double* const* x, const rpcg_opts& o) {
+  for (int i = 0; i < B->count; i++) {
+    rpcg_matrix_t A = B->mats[i];
+    double* hist = o.history ? o.history + (size_t)i * (o.max_iter + 1) : nullptr;
+    B->h_sys[i] = SysDev{A->m, b[i], x[i], A->r, A->d, A->w, A->inv, hist, o.tol, o.max_iter, 0};
+  }
+}
+
 // One launch of the batch graph (set-up + loop) with the given b/x.
 static rpcg_status batch_run(rpcg_batch_t B, const double* const* b, double* const* x, int v, const rpcg_opts& o,
                              int block, int tile, cudaStream_t s) {
   cudaGraphExec_t e = nullptr;
   rpcg_status st = batch_get_graph(B, v, block, tile, &e);
   if (st != RPCG_OK) return st;
-  for (int i = 0; i < B->count; i++) {
-    rpcg_matrix_t A = B->mats[i];
-    double* hist = o.history ? o.history + (size_t)i * (o.max_iter + 1) : nullptr;
-    B->h_sys[i] = SysDev{A->m, b[i], x[i], A->r, A->d, A->w, A->inv, hist, o.tol, o.max_iter, 0};
-  }
+  batch_upload(B, b, x, o);
   RPCG_CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys, B->count * sizeof(SysDev), cudaMemcpyHostToDevice, s));
   RPCG_CUDA_TRY(cudaGraphLaunch(e, s));
   return RPCG_OK;
+}
+
+// The batch loop launched kernel by kernel from the host, with events
+// around each kind of pass (set-up, A, B, C, retire/list): a measurement
+// tool.  Same kernels, same order, same results as the graph.
+template <int V, int BLOCK>
+static rpcg_status batch_eager(rpcg_batch_t B, int tile, cudaStream_t s, float* pass_ms, int32_t* launches) {
+  rpcg_batch_s::Layout* L = nullptr;
+  rpcg_status st = batch_layout(B, tile, &L);
+  if (st != RPCG_OK) return st;
+  BatchPlan P;
+  st = batch_plan<V, BLOCK>(B, L, &P);
+  if (st != RPCG_OK) return st;
+  const BatchDesc D{B->d_sys, B->d_state, B->d_red, B->d_head, B->d_aprefix, L->nunits, L->uprefix, L->partials,
+                    B->count, tile};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  RPCG_CUDA_TRY(cudaEventCreate(&e0));
+  RPCG_CUDA_TRY(cudaEventCreate(&e1));
+  int* h_active = nullptr;
+  cudaError_t err = cudaMallocHost(&h_active, sizeof(int));
+  auto timed = [&](int k, int nl, auto launch) {
+    if (err != cudaSuccess) return;
+    err = cudaEventRecord(e0, s);
+    if (err == cudaSuccess) launch();
+    if (err == cudaSuccess) err = cudaGetLastError();
+    if (err == cudaSuccess) err = cudaEventRecord(e1, s);
+    if (err == cudaSuccess) err = cudaEventSynchronize(e1);
+    float ms = 0.f;
+    if (err == cudaSuccess) err = cudaEventElapsedTime(&ms, e0, e1);
+    pass_ms[k] += ms;
+    if (launches) launches[k] += nl;
+  };
+  auto active = [&]() {
+    if (err == cudaSuccess) err = cudaMemcpyAsync(h_active, &B->d_head->active_count, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (err == cudaSuccess) err = cudaStreamSynchronize(s);
+    return err == cudaSuccess ? *h_active : 0;
+  };
+  const int* ap = B->d_aprefix;
+  timed(0, 3, [&] {
+    k_b_init<<<1, 256, 0, s>>>(D);
+    k_b_inv_q<<<P.g_q, BLOCK, 0, s>>>(D, ap);
+    k_b_setup<V, BLOCK><<<P.g_setup, BLOCK, P.sm3, s>>>(D, ap);
+  });
+  timed(4, 1, [&] { k_b_retire<<<1, 256, 0, s>>>(D); });
+  while (active() > 0) {
+    timed(1, 1, [&] { k_b_pass_a<V, BLOCK><<<P.g_a, BLOCK, P.sm1, s>>>(D); });
+    timed(2, 1, [&] { k_b_pass_b<V, BLOCK><<<P.g_b, BLOCK, P.sm2, s>>>(D); });
+    timed(3, 1, [&] { k_b_pass_c<BLOCK><<<P.g_c, BLOCK, 0, s>>>(D); });
+    timed(4, 1, [&] { k_b_retire<<<1, 256, 0, s>>>(D); });
+  }
+  if (h_active) cudaFreeHost(h_active);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (err != cudaSuccess) {
+    set_error("batch_eager: %s", cudaGetErrorString(err));
+    return RPCG_ERR_CUDA;
+  }
+  return RPCG_OK;
+}
+
+// Read the per-system states after a run and fill `res`; returns the worst status.
+static rpcg_status batch_results(rpcg_batch_t B, double* const* x, const rpcg_opts& opt, rpcg_result* res,
+                                 cudaStream_t s) {
+  RPCG_CUDA_TRY(cudaMemcpyAsync(B->h_state, B->d_state, B->count * sizeof(SysState), cudaMemcpyDeviceToHost, s));
+  RPCG_CUDA_TRY(cudaStreamSynchronize(s));
+  rpcg_status worst = RPCG_OK;
+  for (int i = 0; i < B->count; i++) {
+    const SysState& h = B->h_state[i];
+    const int n = B->mats[i]->m.n;
+    if (n == 0) {
+      res[i] = rpcg_result{0, RPCG_OK, 0.0, 0.0, 0, 0};
+      continue;
+    }
+    if (h.bzero) RPCG_CUDA_TRY(cudaMemsetAsync(x[i], 0, (size_t)n * sizeof(double), s));
+    int status = h.status;
+    if (status == RPCG_OK && !(h.rel < opt.tol)) status = RPCG_NOT_CONVERGED;
+    res[i] = rpcg_result{h.iter, status, h.rel, h.tau, 0, 0};
+    if (status < 0 && (worst >= 0 || status < worst)) worst = (rpcg_status)status;
+    else if (status > 0 && worst == RPCG_OK) worst = (rpcg_status)status;
+  }
+  RPCG_CUDA_TRY(cudaStreamSynchronize(s));
+  return worst;
 }
 
 }  // namespace rpcg
@@ -255,11 +340,11 @@ rpcg_status rpcg_batch_create(rpcg_batch_t* out, int32_t count, const rpcg_matri
   rpcg_batch_t B = new rpcg_batch_s();
   B->count = count;
   B->mats.assign(A, A + count);
-  for (int i = 0; i < count; i++) B->nactive0 += A[i]->m.n > 0 ? 1 : 0;
   cudaError_t e = cudaMalloc(&B->d_sys, count * sizeof(SysDev));
   if (e == cudaSuccess) e = cudaMalloc(&B->d_state, count * sizeof(SysState));
   if (e == cudaSuccess) e = cudaMalloc(&B->d_red, count * sizeof(SysRed));
-  if (e == cudaSuccess) e = cudaMalloc(&B->d_head, sizeof(BatchScratchHead));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_head, sizeof(BatchHead));
+  if (e == cudaSuccess) e = cudaMalloc(&B->d_aprefix, ((size_t)count + 1) * sizeof(int));
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_sys, count * sizeof(SysDev));
   if (e == cudaSuccess) e = cudaMallocHost(&B->h_state, count * sizeof(SysState));
   if (e == cudaSuccess) e = cudaMemset(B->d_red, 0, count * sizeof(SysRed));
@@ -314,7 +399,7 @@ rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double* const* b, double* con
       RPCG_CUDA_TRY(cudaEventCreate(&e1));
       float best = 1e30f;
       for (int cb : {128, 256}) {
-        for (int ct : {2048, 8192, 32768}) {
+        for (int ct : {1024, 4096, 16384}) {
           rpcg_status st = batch_run(B, b, xt.data(), RPCG_EXBLAS, t, cb, ct, s);  // builds the graph (untimed)
           if (st != RPCG_OK) return st;
           RPCG_CUDA_TRY(cudaEventRecord(e0, s));
@@ -339,25 +424,40 @@ rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double* const* b, double* con
   }
   rpcg_status st = batch_run(B, b, x, v, opt, block, tile, s);
   if (st != RPCG_OK) return st;
-  RPCG_CUDA_TRY(cudaMemcpyAsync(B->h_state, B->d_state, B->count * sizeof(SysState), cudaMemcpyDeviceToHost, s));
-  RPCG_CUDA_TRY(cudaStreamSynchronize(s));
-  rpcg_status worst = RPCG_OK;
-  for (int i = 0; i < B->count; i++) {
-    const SysState& h = B->h_state[i];
-    const int n = B->mats[i]->m.n;
-    if (n == 0) {
-      res[i] = rpcg_result{0, RPCG_OK, 0.0, 0.0, 0, 0};
-      continue;
-    }
-    if (h.bzero) RPCG_CUDA_TRY(cudaMemsetAsync(x[i], 0, (size_t)n * sizeof(double), s));
-    int status = h.status;
-    if (status == RPCG_OK && !(h.rel < opt.tol)) status = RPCG_NOT_CONVERGED;
-    res[i] = rpcg_result{h.iter, status, h.rel, h.tau, 0, 0};
-    if (status < 0 && (worst >= 0 || status < worst)) worst = (rpcg_status)status;
-    else if (status > 0 && worst == RPCG_OK) worst = (rpcg_status)status;
-  }
-  RPCG_CUDA_TRY(cudaStreamSynchronize(s));
-  return worst;
+  return batch_results(B, x, opt, res, s);
+}
+
+rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double* const* b, double* const* x, int32_t v,
+                                      const rpcg_opts* o, rpcg_result* res, float* pass_ms, int32_t* launches,
+                                      void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(B != nullptr && b != nullptr && x != nullptr && res != nullptr && pass_ms != nullptr,
+                 "NULL argument");
+  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS, "batched solves support the plain and exblas variants");
+  rpcg_opts opt;
+  if (o) opt = *o;
+  else rpcg_opts_default(&opt);
+  RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
+  RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
+  RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
+  for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int block = opt.block ? opt.block : (B->tuned_block ? B->tuned_block : 128);
+  const int tile = opt.tile ? opt.tile : (B->tuned_tile ? B->tuned_tile : 4096);
+  for (int k = 0; k < 5; k++) pass_ms[k] = 0.f;
+  if (launches)
+    for (int k = 0; k < 5; k++) launches[k] = 0;
+  batch_upload(B, b, x, opt);
+  RPCG_CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys, B->count * sizeof(SysDev), cudaMemcpyHostToDevice, s));
+  rpcg_status st;
+  if (block == 128)
+    st = v == RPCG_PLAIN ? batch_eager<RPCG_PLAIN, 128>(B, tile, s, pass_ms, launches)
+                         : batch_eager<RPCG_EXBLAS, 128>(B, tile, s, pass_ms, launches);
+  else
+    st = v == RPCG_PLAIN ? batch_eager<RPCG_PLAIN, 256>(B, tile, s, pass_ms, launches)
+                         : batch_eager<RPCG_EXBLAS, 256>(B, tile, s, pass_ms, launches);
+  if (st != RPCG_OK) return st;
+  return batch_results(B, x, opt, res, s);
 }
 
 rpcg_status rpcg_batch_tuned(rpcg_batch_t B, int32_t* block, int32_t* tile) {

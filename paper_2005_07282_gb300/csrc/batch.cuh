@@ -1,6 +1,19 @@
 // Device side of the batched solver, shared by the batch API (batch.cu) and
 // the serving loop (server.cu): per-system records, the work-unit driver and
 // the pass kernels.  See batch.cu for the scheme.
+//
+// Work units are ranges of `tile` rows of one system (unit k of system s is
+// rows [k tile, min(n_s, (k+1) tile))).  After the set-up pass and after
+// every iteration a one-block kernel lists the units of the systems still
+// iterating as a prefix over systems (aprefix[s] = index of system s's
+// first unit among the listed ones).  CTAs take chunks of listed units
+// (up to kChunkUnits, one when few are listed) from an atomic work counter,
+// so the work of the systems still iterating is spread over the whole GPU
+// however few they are.  Inside a chunk the consecutive units of one
+// system share the CTA's register windows and shared accumulator; the CTA
+// flushes them once per system and adds the number of units it did to that
+// system's arrival counter; the CTA whose addition completes the system
+// finishes it.
 #pragma once
 #include <climits>
 
@@ -26,15 +39,6 @@ struct SysState {
   int iter, status, bad_row, bzero, active, pad;
 };
 
-struct Unit {
-  int sys, r0, r1;
-};
-
-struct BatchScratchHead {
-  int active_count;
-  int pad;
-};
-
 // per-system reduction scratch (digits, arrival counter, flags)
 struct SysRed {
   unsigned long long digits[3][kNDig];
@@ -42,10 +46,117 @@ struct SysRed {
   unsigned int flags;
 };
 
-static __device__ __forceinline__ void b_stop(SysState* st, BatchScratchHead* head) {
+constexpr int kChunkUnits = 4;  // listed units a CTA takes at a time
+enum { kWorkSetup = 0, kWorkA = 1, kWorkB = 2 };
+
+struct BatchHead {
+  int active_count;  // systems still iterating
+  int pad;
+  unsigned int work[4];  // work counters of the reducing passes
+};
+
+// Everything the kernels need about a batch (passed by value).
+struct BatchDesc {
+  const SysDev* sys;
+  SysState* st;
+  SysRed* red;
+  BatchHead* head;
+  int* aprefix;        // [count + 1] listed units of the iterating systems
+  const int* nunits;   // [count] units of each system
+  const int* uprefix;  // [count + 1] first unit of each system among all units (plain partials), or null
+  double* partials;    // plain variant: per unit, 3 values
+  int count;
+  int tile;
+};
+
+static __device__ __forceinline__ void b_stop(SysState* st, BatchHead* head) {
   if (st->active) {
     st->active = 0;
     atomicSub(&head->active_count, 1);
+  }
+}
+
+// the system of listed unit a: the largest s with prefix[s] <= a (systems
+// with no listed units have prefix[s] == prefix[s + 1] and are skipped)
+__device__ __forceinline__ int unit_system(const int* prefix, int count, int a) {
+  int lo = 0, hi = count - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= a) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Block-wide exclusive scan (blockDim.x a multiple of 32, at most 1024);
+// *total receives the sum over the block.
+static __device__ __forceinline__ int block_exclusive_scan(int v, int* total) {
+  __shared__ int wsum[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) wsum[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? wsum[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, w, o);
+      if (lane >= o) w += y;
+    }
+    wsum[lane] = w;  // inclusive sums of the warp totals
+  }
+  __syncthreads();
+  const int excl = x - v + (wid ? wsum[wid - 1] : 0);
+  *total = wsum[nw - 1];
+  __syncthreads();  // wsum may be reused
+  return excl;
+}
+
+// One block: list the units of the systems that take part (every system
+// with rows when `setup`, else the systems still iterating) as a prefix
+// over systems.  Systems are split into contiguous per-thread ranges so the
+// listing keeps system order.
+static __device__ void build_prefix(const BatchDesc& B, bool setup) {
+  const int T = blockDim.x;
+  const int per = (B.count + T - 1) / T;
+  const int lo = min(B.count, (int)threadIdx.x * per), hi = min(B.count, lo + per);
+  auto units_of = [&](int s) { return (setup ? B.sys[s].m.n > 0 : B.st[s].active != 0) ? B.nunits[s] : 0; };
+  int sum = 0;
+  for (int s = lo; s < hi; s++) sum += units_of(s);
+  int total = 0;
+  int run = block_exclusive_scan(sum, &total);
+  for (int s = lo; s < hi; s++) {
+    B.aprefix[s] = run;
+    run += units_of(s);
+  }
+  if (threadIdx.x == 0) B.aprefix[B.count] = total;
+}
+
+// ------------------------------------------------------------------ L2 prefetch
+//
+// Each warp of a reducing pass works on 32 consecutive rows per step; its
+// lane 0 asks the copy engine to bring the rows of kPfSteps steps later
+// into L2 (cp.async.bulk.prefetch: a hint that changes no value), so the
+// DRAM stream does not wait for the threads' own loads to be issued.
+
+constexpr int kPfSteps = 2;
+
+__device__ __forceinline__ void l2_prefetch(const void* p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(__cvta_generic_to_global(p)), "r"(bytes) : "memory");
+}
+
+// the SELL-32 slab (values and columns) of the slice holding `row`
+__device__ __forceinline__ void l2_prefetch_slice(const MatDev& m, int row) {
+  const int sl = row >> 5;
+  const long long so = __ldg(m.sptr + sl), se = __ldg(m.sptr + sl + 1);
+  if (se > so) {
+    l2_prefetch(m.val + so, (unsigned)((se - so) * 8));
+    l2_prefetch(m.col + so, (unsigned)((se - so) * 4));
   }
 }
 
@@ -56,144 +167,206 @@ struct UnitSmem {
   long long dig[kNDig];
   uint32_t D[kNDig];
   double value[3];
+  int base;
   bool last;
 };
 
-// Process every unit of the active systems.  row_fn(sys, row, R, sacc)
-// deposits into the reducer; fin_fn(sys, values) runs in thread 0 of the
-// CTA that completes a system.  `need_active` = 0 processes every system
-// (the set-up pass).
-template <int V, int NACC, int BLOCK, class RowFn, class FinFn>
-__device__ __forceinline__ void for_units(const Unit* __restrict__ units, const int* __restrict__ nunits_p,
-                                          const int* __restrict__ unit_count,
-                                          SysState* states, SysRed* red, double* unit_partials, bool need_active,
-                                          unsigned char* smem, RowFn row_fn, FinFn fin_fn) {
+// the unit prefix is copied to shared memory for batches of up to
+// kPrefixSmem - 1 systems; larger ones search it in global memory
+constexpr int kPrefixSmem = 1024;
+
+template <int V>
+__host__ __device__ constexpr size_t b_smem(int nacc, int count) {
+  return (V == RPCG_EXBLAS ? (size_t)nacc * kNDig * kCopies * 8 : 0) + sizeof(UnitSmem) +
+         (size_t)(count + 1 <= kPrefixSmem ? count + 1 : 0) * 4 + 16;
+}
+
+// Process the listed units of `prefix`, taking chunks from *work.
+// row_fn(sys, row, dep) deposits dep(j, a, b) into dot j; fin_fn(sys, values)
+// runs in thread 0 of the CTA that completes a system.
+template <int V, int NACC, int BLOCK, class PfFn, class RowFn, class FinFn>
+__device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restrict__ prefix, unsigned int* work,
+                                          unsigned char* smem, PfFn pf_fn, RowFn row_fn, FinFn fin_fn) {
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem);
   UnitSmem* us = reinterpret_cast<UnitSmem*>(smem + (V == RPCG_EXBLAS ? NACC * kNDig * kCopies * 8 : 0));
   const int copy = threadIdx.x & (kCopies - 1);
-  const int nunits = *nunits_p;
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const Unit U = units[u];
-    if (need_active && !states[U.sys].active) continue;  // uniform over the CTA
-    Window win[NACC];
-    double acc[NACC];
-    bool bad = false;
-#pragma unroll
-    for (int j = 0; j < NACC; j++) {
-      window_init(win[j]);
-      acc[j] = 0.0;
-    }
-    if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc, NACC);
+  const int* sp = prefix;
+  if (B.count + 1 <= kPrefixSmem) {
+    int* cp = reinterpret_cast<int*>(us + 1);
+    for (int i = threadIdx.x; i <= B.count; i += BLOCK) cp[i] = prefix[i];
+    sp = cp;
+  }
+  __syncthreads();
+  const int total = sp[B.count];
+  // chunks of up to kChunkUnits units while there is plenty of work; single
+  // units when few are listed, so they spread over every CTA
+  const int chunk = max(1, min(kChunkUnits, total / (2 * (int)gridDim.x)));
+  for (;;) {
+    if (threadIdx.x == 0) us->base = (int)atomicAdd(work, (unsigned)chunk);
     __syncthreads();
-    for (int row = U.r0 + threadIdx.x; row < U.r1; row += BLOCK) {
-      row_fn(U.sys, row, [&](int j, double a, double b) {
-        if constexpr (V == RPCG_EXBLAS) {
-          const ExactProd e = exact_product(a, b);
-          bad |= e.bad;
-          exact_deposit(win[j], sacc + j * kNDig * kCopies, copy, e);
-        } else {
-          acc[j] = __fma_rn(a, b, acc[j]);
-        }
-      });
-    }
-    SysRed* R = red + U.sys;
-    if constexpr (V == RPCG_EXBLAS) {
-#pragma unroll
-      for (int j = 0; j < NACC; j++) window_flush(win[j], sacc + j * kNDig * kCopies, copy);
-      if (bad) atomicOr(&R->flags, 1u);
-      __syncthreads();
-      for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, R->digits[j]);
-    } else {
-      for (int j = 0; j < NACC; j++) {
-        const double sblk = block_sum_fixed<BLOCK>(acc[j], us->sw);
-        if (threadIdx.x == 0) unit_partials[(size_t)u * 3 + j] = sblk;
-      }
-    }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      __threadfence();
-      const unsigned int prev = atomicAdd(&R->counter, 1u);
-      us->last = (prev == (unsigned)unit_count[U.sys] - 1u);
-    }
-    __syncthreads();
-    if (us->last) {
-      __threadfence();
+    const int base = us->base;
+    __syncthreads();  // everyone has read base
+    if (base >= total) break;
+    const int end = min(base + chunk, total);
+    for (int a = base; a < end;) {
+      const int s = unit_system(sp, B.count, a);
+      const int run_end = min(end, sp[s + 1]);
+      const int k0 = a - sp[s], k1 = k0 + (run_end - a);  // units [k0, k1) of system s
+      const int n = B.sys[s].m.n;
+      SysRed* R = B.red + s;
       if constexpr (V == RPCG_EXBLAS) {
-        for (int j = 0; j < NACC; j++) {
-          for (int k = threadIdx.x; k < kNDig; k += BLOCK) us->dig[k] = (long long)atomicExch(&R->digits[j][k], 0ull);
-          __syncthreads();
-          if (threadIdx.x == 0) us->value[j] = round_digits(us->dig, us->D);
-          __syncthreads();
+        Window win[NACC];
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < NACC; j++) window_init(win[j]);
+        smem_acc_zero(sacc, NACC);
+        __syncthreads();
+        const int r0 = k0 * B.tile, r1 = min(n, k1 * B.tile);
+        for (int row = r0 + threadIdx.x; row < r1; row += BLOCK) {
+          const int ahead = row + kPfSteps * BLOCK;
+          if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(s, ahead, r1);
+          row_fn(s, row, [&](int j, double x, double y) {
+            const ExactProd e = exact_product(x, y);
+            bad |= e.bad;
+            exact_deposit(win[j], sacc + j * kNDig * kCopies, copy, e);
+          });
         }
-        if (threadIdx.x == 0) {
-          const unsigned int f = atomicExch(&R->flags, 0u);
-          if (f & 1u)
-            for (int j = 0; j < NACC; j++) us->value[j] = __longlong_as_double(0x7FF8000000000000ll);
-        }
+#pragma unroll
+        for (int j = 0; j < NACC; j++) window_flush(win[j], sacc + j * kNDig * kCopies, copy);
+        if (bad) atomicOr(&R->flags, 1u);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, R->digits[j]);
       } else {
-        if (threadIdx.x == 0) {
-          // the system's units are contiguous: sum their partials in unit order
-          int first = u;
-          while (first > 0 && units[first - 1].sys == U.sys) first--;
+        // plain: one fixed-order partial per unit, summed in unit order at the end
+        for (int k = k0; k < k1; k++) {
+          double acc[NACC];
+#pragma unroll
+          for (int j = 0; j < NACC; j++) acc[j] = 0.0;
+          const int r0 = k * B.tile, r1 = min(n, (k + 1) * B.tile);
+          for (int row = r0 + threadIdx.x; row < r1; row += BLOCK) {
+            const int ahead = row + kPfSteps * BLOCK;
+            if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(s, ahead, r1);
+            row_fn(s, row, [&](int j, double x, double y) { acc[j] = __fma_rn(x, y, acc[j]); });
+          }
+#pragma unroll
           for (int j = 0; j < NACC; j++) {
-            double v = 0.0;
-            for (int k = 0; k < unit_count[U.sys]; k++) v = __dadd_rn(v, __ldcg(&unit_partials[(size_t)(first + k) * 3 + j]));
-            us->value[j] = v;
+            const double sblk = block_sum_fixed<BLOCK>(acc[j], us->sw);
+            if (threadIdx.x == 0) B.partials[(size_t)(B.uprefix[s] + k) * 3 + j] = sblk;
           }
         }
+        __threadfence();
       }
+      __syncthreads();
       if (threadIdx.x == 0) {
-        R->counter = 0;
-        fin_fn(U.sys, us->value);
+        __threadfence();
+        const unsigned int cnt = (unsigned)(k1 - k0);
+        const unsigned int prev = atomicAdd(&R->counter, cnt);
+        us->last = (prev + cnt == (unsigned)B.nunits[s]);
       }
+      __syncthreads();
+      if (us->last) {
+        __threadfence();
+        if constexpr (V == RPCG_EXBLAS) {
+#pragma unroll
+          for (int j = 0; j < NACC; j++) {
+            for (int k = threadIdx.x; k < kNDig; k += BLOCK) us->dig[k] = (long long)atomicExch(&R->digits[j][k], 0ull);
+            __syncthreads();
+            if (threadIdx.x == 0) us->value[j] = round_digits(us->dig, us->D);
+            __syncthreads();
+          }
+          if (threadIdx.x == 0) {
+            const unsigned int f = atomicExch(&R->flags, 0u);
+            if (f & 1u)
+              for (int j = 0; j < NACC; j++) us->value[j] = __longlong_as_double(0x7FF8000000000000ll);
+          }
+        } else {
+          if (threadIdx.x == 0) {
+            for (int j = 0; j < NACC; j++) {
+              double v = 0.0;
+              for (int k = 0; k < B.nunits[s]; k++) v = __dadd_rn(v, __ldcg(&B.partials[(size_t)(B.uprefix[s] + k) * 3 + j]));
+              us->value[j] = v;
+            }
+          }
+        }
+        if (threadIdx.x == 0) {
+          R->counter = 0;
+          fin_fn(s, us->value);
+        }
+      }
+      __syncthreads();
+      a = run_end;
     }
-    __syncthreads();
   }
-}
-
-template <int V>
-__host__ __device__ constexpr size_t b_smem(int nacc) {
-  return (V == RPCG_EXBLAS ? (size_t)nacc * kNDig * kCopies * 8 : 0) + sizeof(UnitSmem) + 16;
 }
 
 // ------------------------------------------------------------------ kernels
 
-static __global__ void k_b_init(const SysDev* __restrict__ sys, SysState* st, BatchScratchHead* head, int count,
-                                int nactive) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
-    SysState& t = st[s];
+// Reset the states of every system with rows, list their units, clear the
+// work counters (one block).
+static __global__ void k_b_init(BatchDesc B) {
+  for (int s = threadIdx.x; s < B.count; s += blockDim.x) {
+    SysState& t = B.st[s];
     t.rho = t.beta = t.beta_old = t.gamma = t.bnorm = 0.0;
     t.tau = t.rel = __longlong_as_double(0x7FF8000000000000ll);
     t.iter = 0;
     t.status = 0;
     t.bad_row = INT_MAX;
     t.bzero = 0;
-    t.active = sys[s].m.n > 0 ? 1 : 0;  // an empty system has no units: done at once
+    t.active = B.sys[s].m.n > 0 ? 1 : 0;  // an empty system has no units: done at once
     t.pad = 0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) head->active_count = nactive;
+  __shared__ int nact;
+  if (threadIdx.x == 0) nact = 0;
+  __syncthreads();
+  for (int s = threadIdx.x; s < B.count; s += blockDim.x)
+    if (B.sys[s].m.n > 0) atomicAdd(&nact, 1);
+  build_prefix(B, true);
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    B.head->active_count = nact;
+    for (int k = 0; k < 4; k++) B.head->work[k] = 0u;
+  }
 }
 
-// inverse diagonal and A x0 for every unit
-static __global__ void k_b_inv_q(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                 const int* __restrict__ nunits_p, SysState* st) {
-  const int nunits = *nunits_p;
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const Unit U = units[u];
-    const SysDev& S = sys[U.sys];
-    for (int i = U.r0 + threadIdx.x; i < U.r1; i += blockDim.x) {
+// Reset the listed (newly admitted) systems' states (serving loop).
+static __global__ void k_b_init_list(BatchDesc B, const int* __restrict__ list, int nlist) {
+  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlist; k += gridDim.x * blockDim.x) {
+    const int s = list[k];
+    SysState& t = B.st[s];
+    t.rho = t.beta = t.beta_old = t.gamma = t.bnorm = 0.0;
+    t.tau = t.rel = __longlong_as_double(0x7FF8000000000000ll);
+    t.iter = 0;
+    t.status = 0;
+    t.bad_row = INT_MAX;
+    t.bzero = 0;
+    t.active = B.sys[s].m.n > 0 ? 1 : 0;
+    if (t.active) atomicAdd(&B.head->active_count, 1);
+    t.pad = 0;
+  }
+}
+
+// Inverse diagonal and A x0 for the listed units (no reduction: static split).
+static __global__ void k_b_inv_q(BatchDesc B, const int* __restrict__ prefix) {
+  const int total = prefix[B.count];
+  for (int a = blockIdx.x; a < total; a += gridDim.x) {
+    const int s = unit_system(prefix, B.count, a);
+    const SysDev& S = B.sys[s];
+    const int k = a - prefix[s];
+    const int r1 = min(S.m.n, (k + 1) * B.tile);
+    for (int i = k * B.tile + threadIdx.x; i < r1; i += blockDim.x) {
       double aii = 0.0;
       bool found = false;
       const int len = S.m.rowptr[i + 1] - S.m.rowptr[i];
       const long long base = sell_index(S.m, i, 0);
-      for (int k = 0; k < len; k++) {
-        if (S.m.col[base + 32ll * k] == i) {
-          aii = S.m.val[base + 32ll * k];
+      for (int q = 0; q < len; q++) {
+        if (S.m.col[base + 32ll * q] == i) {
+          aii = S.m.val[base + 32ll * q];
           found = true;
         }
       }
       if (!found || !(aii > 0.0)) {
-        atomicMin(&st[U.sys].bad_row, i);
+        atomicMin(&B.st[s].bad_row, i);
         S.inv[i] = 0.0;
       } else {
         S.inv[i] = __drcp_rn(aii);
@@ -204,15 +377,12 @@ static __global__ void k_b_inv_q(const SysDev* __restrict__ sys, const Unit* __r
 }
 
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_setup(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                   const int* __restrict__ nunits, const int* __restrict__ unit_count,
-                                                   SysState* st, SysRed* red, double* unit_partials,
-                                                   BatchScratchHead* head) {
+__global__ void __launch_bounds__(BLOCK) k_b_setup(BatchDesc B, const int* __restrict__ prefix) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 3, BLOCK>(
-      units, nunits, unit_count, st, red, unit_partials, false, smem,
+      B, prefix, &B.head->work[kWorkSetup], smem, [](int, int, int) {},
       [&](int s, int i, auto dep) {
-        const SysDev& S = sys[s];
+        const SysDev& S = B.sys[s];
         const double bi = S.b[i];
         const double ri = __dsub_rn(bi, S.w[i]);
         const double zi = __dmul_rn(S.inv[i], ri);
@@ -223,8 +393,8 @@ __global__ void __launch_bounds__(BLOCK) k_b_setup(const SysDev* __restrict__ sy
         dep(2, bi, bi);
       },
       [&](int s, const double* v) {
-        SysState* t = st + s;
-        const SysDev& S = sys[s];
+        SysState* t = B.st + s;
+        const SysDev& S = B.sys[s];
         if (t->bad_row < S.m.n) {
           const int i = t->bad_row;
           double aii = 0.0;
@@ -233,12 +403,12 @@ __global__ void __launch_bounds__(BLOCK) k_b_setup(const SysDev* __restrict__ sy
           for (int k = 0; k < len; k++)
             if (S.m.col[base + 32ll * k] == i) aii = S.m.val[base + 32ll * k];
           t->status = isfinite(aii) ? RPCG_ERR_NOT_SPD : RPCG_ERR_NONFINITE;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         if (!isfinite(v[0]) || !isfinite(v[1]) || !isfinite(v[2])) {
           t->status = RPCG_ERR_NONFINITE;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         t->beta = v[0];
@@ -250,41 +420,39 @@ __global__ void __launch_bounds__(BLOCK) k_b_setup(const SysDev* __restrict__ sy
           t->rel = 0.0;
           t->tau = 0.0;
           if (hist) hist[0] = 0.0;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         t->tau = v[1];
         t->rel = __ddiv_rn(__dsqrt_rn(v[1]), bnorm);
         if (hist) hist[0] = t->rel;
-        if (!((t->rel >= S.tol) && (0 < S.max_iter))) b_stop(t, head);
+        if (!((t->rel >= S.tol) && (0 < S.max_iter))) b_stop(t, B.head);
       });
 }
 
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_pass_a(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                    const int* __restrict__ nunits, const int* __restrict__ unit_count,
-                                                    SysState* st, SysRed* red, double* unit_partials,
-                                                    BatchScratchHead* head) {
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_a(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 1, BLOCK>(
-      units, nunits, unit_count, st, red, unit_partials, true, smem,
+      B, B.aprefix, &B.head->work[kWorkA], smem,
+      [&](int s, int i, int) { l2_prefetch_slice(B.sys[s].m, i); },
       [&](int s, int i, auto dep) {
-        const SysDev& S = sys[s];
+        const SysDev& S = B.sys[s];
         const double v = sell_row(S.m, i, S.d);
         S.w[i] = v;
         dep(0, __ldg(S.d + i), v);
       },
       [&](int s, const double* v) {
-        SysState* t = st + s;
+        SysState* t = B.st + s;
         const double dw = v[0];
         if (!isfinite(dw)) {
           t->status = RPCG_ERR_NONFINITE;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         if (!(dw > 0.0)) {
           t->status = RPCG_ERR_NOT_SPD;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         t->beta_old = t->beta;
@@ -293,16 +461,15 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_a(const SysDev* __restrict__ s
 }
 
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_pass_b(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                    const int* __restrict__ nunits, const int* __restrict__ unit_count,
-                                                    SysState* st, SysRed* red, double* unit_partials,
-                                                    BatchScratchHead* head) {
+__global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 2, BLOCK>(
-      units, nunits, unit_count, st, red, unit_partials, true, smem,
+      B, B.aprefix, &B.head->work[kWorkB], smem, [](int, int, int) {},
       [&](int s, int i, auto dep) {
-        const SysDev& S = sys[s];
-        const double rho = st[s].rho;
+        const SysDev& S = B.sys[s];
+        const SysState& t = B.st[s];
+        if (t.status != 0) return;  // stopped in pass A of this iteration
+        const double rho = t.rho;
         const double di = S.d[i], wi = S.w[i];
         const double xi = __fma_rn(rho, di, S.x[i]);
         const double ri = __fma_rn(-rho, wi, S.r[i]);
@@ -313,15 +480,16 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(const SysDev* __restrict__ s
         dep(1, ri, ri);
       },
       [&](int s, const double* v) {
-        SysState* t = st + s;
-        const SysDev& S = sys[s];
+        SysState* t = B.st + s;
+        if (t->status != 0) return;
+        const SysDev& S = B.sys[s];
         const double beta = v[0], tau = v[1];
         t->beta = beta;
         t->tau = tau;
         if (!isfinite(beta) || !isfinite(tau)) {
           t->status = RPCG_ERR_NONFINITE;
           t->iter += 1;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         t->gamma = __ddiv_rn(beta, t->beta_old);
@@ -330,7 +498,7 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(const SysDev* __restrict__ s
         if (S.history) S.history[t->iter] = t->rel;
         if (tau > 0.0 && !(beta > 0.0)) {
           t->status = RPCG_ERR_NOT_SPD;
-          b_stop(t, head);
+          b_stop(t, B.head);
           return;
         }
         if (!((t->rel >= S.tol) && (t->iter < S.max_iter))) {
@@ -339,61 +507,48 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(const SysDev* __restrict__ s
       });
 }
 
-// S7 for every system that ran pass B this iteration; systems that finished
-// in pass B leave the active set here.
+// S7 for every listed system that is still running (no reduction: static split).
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_b_pass_c(const SysDev* __restrict__ sys, const Unit* __restrict__ units,
-                                                    const int* __restrict__ nunits_p, SysState* st) {
-  const int nunits = *nunits_p;
-  for (int u = blockIdx.x; u < nunits; u += gridDim.x) {
-    const Unit U = units[u];
-    const SysState& t = st[U.sys];
+__global__ void __launch_bounds__(BLOCK) k_b_pass_c(BatchDesc B) {
+  const int* prefix = B.aprefix;
+  const int total = prefix[B.count];
+  for (int a = blockIdx.x; a < total; a += gridDim.x) {
+    const int s = unit_system(prefix, B.count, a);
+    const SysState& t = B.st[s];
     if (!t.active || t.status != 0) continue;
-    const SysDev& S = sys[U.sys];
+    const SysDev& S = B.sys[s];
     const double g = t.gamma;
-    for (int i = U.r0 + threadIdx.x; i < U.r1; i += BLOCK) {
+    const int k = a - prefix[s];
+    const int r1 = min(S.m.n, (k + 1) * B.tile);
+    for (int i = k * B.tile + threadIdx.x; i < r1; i += BLOCK) {
       const double zi = __dmul_rn(S.inv[i], S.r[i]);
       S.d[i] = __fma_rn(g, S.d[i], zi);
     }
   }
 }
 
-// Retire the systems that finished in pass B and set the loop condition.
-static __global__ void k_b_cond(SysState* st, int count, BatchScratchHead* head, cudaGraphConditionalHandle cond) {
-  for (int s = threadIdx.x; s < count; s += blockDim.x) {
-    if (st[s].active == 2) b_stop(st + s, head);
+// One block, after pass C: retire the systems that finished in pass B, list
+// the units of the systems still iterating, clear the work counters; with a
+// graph conditional handle, set the while node's condition.
+static __device__ void retire_and_list(BatchDesc B) {
+  for (int s = threadIdx.x; s < B.count; s += blockDim.x) {
+    if (B.st[s].active == 2 || (B.st[s].active && B.st[s].status != 0)) b_stop(B.st + s, B.head);
   }
   __syncthreads();
+  build_prefix(B, false);
+  __syncthreads();
   if (threadIdx.x == 0) {
+    for (int k = 0; k < 4; k++) B.head->work[k] = 0u;
     __threadfence();
-    cudaGraphSetConditional(cond, atomicAdd(&head->active_count, 0) > 0 ? 1u : 0u);
   }
 }
 
-// Retire the systems that finished in pass B (the serving loop's form of
-// k_b_cond: the host reads the states between chunks of iterations).
-static __global__ void k_b_retire(SysState* st, int count, BatchScratchHead* head) {
-  for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < count; s += gridDim.x * blockDim.x) {
-    if (st[s].active == 2) b_stop(st + s, head);
-  }
+static __global__ void k_b_cond(BatchDesc B, cudaGraphConditionalHandle cond) {
+  retire_and_list(B);
+  if (threadIdx.x == 0) cudaGraphSetConditional(cond, atomicAdd(&B.head->active_count, 0) > 0 ? 1u : 0u);
 }
 
-// Reset the states of the listed systems (newly admitted ones).
-static __global__ void k_b_init_list(const int* __restrict__ list, int nlist, const SysDev* __restrict__ sys,
-                                     SysState* st, BatchScratchHead* head) {
-  for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < nlist; k += gridDim.x * blockDim.x) {
-    const int s = list[k];
-    SysState& t = st[s];
-    t.rho = t.beta = t.beta_old = t.gamma = t.bnorm = 0.0;
-    t.tau = t.rel = __longlong_as_double(0x7FF8000000000000ll);
-    t.iter = 0;
-    t.status = 0;
-    t.bad_row = INT_MAX;
-    t.bzero = 0;
-    t.active = sys[s].m.n > 0 ? 1 : 0;
-    if (t.active) atomicAdd(&head->active_count, 1);
-    t.pad = 0;
-  }
-}
+// The serving loop's form (the host reads the states between chunks).
+static __global__ void k_b_retire(BatchDesc B) { retire_and_list(B); }
 
 }  // namespace rpcg

@@ -101,15 +101,13 @@ struct rpcg_server_s {
   rpcg::SysState* d_state = nullptr;
   rpcg::SysState* h_state = nullptr;
   rpcg::SysRed* d_red = nullptr;
-  rpcg::BatchScratchHead* d_head = nullptr;
-  rpcg::Unit* d_units = nullptr;
-  rpcg::Unit* d_setup_units = nullptr;
-  int* d_unit_count = nullptr;
-  int* d_counts = nullptr;  // [2]: running units, set-up units
-  int* h_counts = nullptr;
-  double* d_partials = nullptr;
+  rpcg::BatchHead* d_head = nullptr;
+  int* d_aprefix = nullptr;  // [max_slots + 1] units of the iterating systems (built on the device)
+  int* d_sprefix = nullptr;  // [max_slots + 1] units of the newly admitted systems (built here)
+  int* h_sprefix = nullptr;
+  int* d_nunits = nullptr;  // [max_slots]
+  int* h_nunits = nullptr;
   int* d_list = nullptr;
-  int unit_cap = 0;
   int grid_setup = 1, grid_a = 1, grid_b = 1, grid_c = 1, grid_q = 1;
 
   // statistics
@@ -176,9 +174,7 @@ static void serve_loop(rpcg_server_t S) {
   SysDev* sys = S->d_sys;
   SysState* sst = S->d_state;
   SysRed* red = S->d_red;
-  BatchScratchHead* head = S->d_head;
-  int* d_nrun = S->d_counts;
-  int* d_nsetup = S->d_counts + 1;
+  BatchHead* head = S->d_head;
   std::vector<int> running;  // slots being iterated
   for (;;) {
     // ---- admission (FIFO: stop at the first request that does not fit yet).
@@ -292,74 +288,63 @@ static void serve_loop(rpcg_server_t S) {
                             B + 5 * (size_t)n, nullptr, r.tol, r.max_iter, 0};
       fresh.push_back(si);
     }
-    // ---- upload the system table and unit lists; run set-up and a chunk
+    // ---- upload the new systems; run their set-up and a chunk of iterations
     bool ok = true;
     if (!fresh.empty() || !running.empty()) {
-      std::vector<Unit> units, setup_units;
-      std::vector<int> counts(S->max_slots, 0);
-      for (int si : fresh) running.push_back(si);
-      for (int si : running) {
-        const int n = S->slots[si].req.n;
-        const bool is_new = std::find(fresh.begin(), fresh.end(), si) != fresh.end();
-        for (int r0 = 0; r0 < n; r0 += kServeTile) {
-          const Unit u{si, r0, std::min(n, r0 + kServeTile)};
-          units.push_back(u);
-          if (is_new) setup_units.push_back(u);
-          counts[si]++;
-        }
-      }
-      if ((int)units.size() > S->unit_cap) {
-        // more rows than the unit table holds: cannot happen within the budget
-        // (unit_cap is sized from it), but never overrun the table
-        units.resize(S->unit_cap);
-        ok = false;
-      }
-      S->h_counts[0] = (int)units.size();
-      S->h_counts[1] = (int)setup_units.size();
       cudaError_t e = cudaSuccess;
+      const BatchDesc D{sys, sst, red, head, S->d_aprefix, S->d_nunits, nullptr, nullptr, S->max_slots, kServeTile};
+      constexpr int B = kServeBlock;
       if (!fresh.empty()) {
-        for (int si : fresh)
-          e = e == cudaSuccess ? cudaMemcpyAsync(S->d_sys + si, S->h_sys + si, sizeof(SysDev), cudaMemcpyHostToDevice, s) : e;
+        std::fill(S->h_sprefix, S->h_sprefix + S->max_slots + 1, 0);
+        for (int si : fresh) {
+          S->h_nunits[si] = (int)(((long long)S->slots[si].req.n + kServeTile - 1) / kServeTile);
+          S->h_sprefix[si + 1] = S->h_nunits[si];
+        }
+        for (int i = 0; i < S->max_slots; i++) S->h_sprefix[i + 1] += S->h_sprefix[i];
+        for (int si : fresh) {
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->d_sys + si, S->h_sys + si, sizeof(SysDev), cudaMemcpyHostToDevice, s);
+          if (e == cudaSuccess)
+            e = cudaMemcpyAsync(S->d_nunits + si, S->h_nunits + si, sizeof(int), cudaMemcpyHostToDevice, s);
+        }
         if (e == cudaSuccess)
           e = cudaMemcpyAsync(S->d_list, fresh.data(), fresh.size() * sizeof(int), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess)
+          e = cudaMemcpyAsync(S->d_sprefix, S->h_sprefix, (S->max_slots + 1) * sizeof(int), cudaMemcpyHostToDevice, s);
+        const int* sp = S->d_sprefix;
+        if (e == cudaSuccess) {
+          e = launch_check([&] {
+            k_b_init_list<<<1, 256, 0, s>>>(D, S->d_list, (int)fresh.size());
+            k_b_inv_q<<<S->grid_q, B, 0, s>>>(D, sp);
+            k_b_setup<RPCG_EXBLAS, B><<<S->grid_setup, B, b_smem<RPCG_EXBLAS>(3, S->max_slots), s>>>(D, sp);
+            k_b_retire<<<1, 256, 0, s>>>(D);  // lists the units of every system now iterating
+          });
+        }
+        for (int si : fresh) running.push_back(si);
       }
-      if (e == cudaSuccess && !units.empty())
-        e = cudaMemcpyAsync(S->d_units, units.data(), units.size() * sizeof(Unit), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess && !setup_units.empty())
-        e = cudaMemcpyAsync(S->d_setup_units, setup_units.data(), setup_units.size() * sizeof(Unit),
-                            cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess)
-        e = cudaMemcpyAsync(S->d_unit_count, counts.data(), counts.size() * sizeof(int), cudaMemcpyHostToDevice, s);
-      if (e == cudaSuccess) e = cudaMemcpyAsync(S->d_counts, S->h_counts, 2 * sizeof(int), cudaMemcpyHostToDevice, s);
-      Unit* uall = S->d_units;
-      Unit* unew = S->d_setup_units;
-      int* ucount = S->d_unit_count;
-      double* part = S->d_partials;
-      constexpr int B = kServeBlock;
-      if (e == cudaSuccess && !fresh.empty()) {
-        e = launch_check([&] {
-          k_b_init_list<<<1, 256, 0, s>>>(S->d_list, (int)fresh.size(), sys, sst, head);
-          k_b_inv_q<<<S->grid_q, B, 0, s>>>(sys, unew, d_nsetup, sst);
-          k_b_setup<RPCG_EXBLAS, B><<<S->grid_setup, B, b_smem<RPCG_EXBLAS>(3), s>>>(sys, unew, d_nsetup, ucount, sst,
-                                                                                  red, part, head);
-        });
-      }
-      if (e == cudaSuccess && !units.empty()) {
+      if (e == cudaSuccess) {
         e = launch_check([&] {
           for (int k = 0; k < kChunk; k++) {
-            k_b_pass_a<RPCG_EXBLAS, B><<<S->grid_a, B, b_smem<RPCG_EXBLAS>(1), s>>>(sys, uall, d_nrun, ucount, sst, red,
-                                                                                 part, head);
-            k_b_pass_b<RPCG_EXBLAS, B><<<S->grid_b, B, b_smem<RPCG_EXBLAS>(2), s>>>(sys, uall, d_nrun, ucount, sst, red,
-                                                                                 part, head);
-            k_b_pass_c<B><<<S->grid_c, B, 0, s>>>(sys, uall, d_nrun, sst);
-            k_b_retire<<<(S->max_slots + 255) / 256, 256, 0, s>>>(sst, S->max_slots, head);
+            k_b_pass_a<RPCG_EXBLAS, B><<<S->grid_a, B, b_smem<RPCG_EXBLAS>(1, S->max_slots), s>>>(D);
+            k_b_pass_b<RPCG_EXBLAS, B><<<S->grid_b, B, b_smem<RPCG_EXBLAS>(2, S->max_slots), s>>>(D);
+            k_b_pass_c<B><<<S->grid_c, B, 0, s>>>(D);
+            k_b_retire<<<1, 256, 0, s>>>(D);
           }
         });
       }
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(S->h_state, S->d_state, S->max_slots * sizeof(SysState), cudaMemcpyDeviceToHost, s);
       if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      if (e != cudaSuccess) ok = false;
+      if (e != cudaSuccess) {
+        ok = false;
+        cudaGetLastError();
+        // every running request fails below; start the device records afresh
+        cudaMemsetAsync(S->d_state, 0, S->max_slots * sizeof(SysState), s);
+        cudaMemsetAsync(S->d_red, 0, S->max_slots * sizeof(SysRed), s);
+        cudaMemsetAsync(S->d_head, 0, sizeof(BatchHead), s);
+        cudaMemsetAsync(S->d_aprefix, 0, (S->max_slots + 1) * sizeof(int), s);
+        cudaStreamSynchronize(s);
+      }
       S->n_chunks++;
     }
     // ---- retire the systems that stopped (or everything, after an error)
@@ -407,10 +392,6 @@ rpcg_status rpcg_server_create(rpcg_server_t* out, size_t hbm_budget_bytes, int3
   S->max_slots = max_slots;
   S->slots.resize(max_slots);
   cudaGetDevice(&S->device);
-  // unit table: every running row belongs to a slot whose vectors count
-  // against the budget (48 bytes per row), so this bounds the units
-  const size_t cap = (size_t)max_slots + hbm_budget_bytes / (48 * (size_t)kServeTile) + 64;
-  S->unit_cap = (int)std::min<size_t>(cap, (size_t)1 << 22);
   cudaError_t e = cudaStreamCreateWithFlags(&S->stream, cudaStreamNonBlocking);
   if (e == cudaSuccess) e = cudaMalloc(&S->d_sys, max_slots * sizeof(SysDev));
   if (e == cudaSuccess) e = cudaMallocHost(&S->h_sys, max_slots * sizeof(SysDev));
@@ -418,14 +399,15 @@ rpcg_status rpcg_server_create(rpcg_server_t* out, size_t hbm_budget_bytes, int3
   if (e == cudaSuccess) e = cudaMallocHost(&S->h_state, max_slots * sizeof(SysState));
   if (e == cudaSuccess) e = cudaMalloc(&S->d_red, max_slots * sizeof(SysRed));
   if (e == cudaSuccess) e = cudaMemset(S->d_red, 0, max_slots * sizeof(SysRed));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_head, sizeof(BatchScratchHead));
-  if (e == cudaSuccess) e = cudaMemset(S->d_head, 0, sizeof(BatchScratchHead));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_units, (size_t)S->unit_cap * sizeof(Unit));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_setup_units, (size_t)S->unit_cap * sizeof(Unit));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_unit_count, max_slots * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_counts, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMallocHost(&S->h_counts, 2 * sizeof(int));
-  if (e == cudaSuccess) e = cudaMalloc(&S->d_partials, (size_t)S->unit_cap * 3 * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_head, sizeof(BatchHead));
+  if (e == cudaSuccess) e = cudaMemset(S->d_head, 0, sizeof(BatchHead));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_aprefix, ((size_t)max_slots + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(S->d_aprefix, 0, ((size_t)max_slots + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_sprefix, ((size_t)max_slots + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_sprefix, ((size_t)max_slots + 1) * sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&S->d_nunits, max_slots * sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(S->d_nunits, 0, max_slots * sizeof(int));
+  if (e == cudaSuccess) e = cudaMallocHost(&S->h_nunits, max_slots * sizeof(int));
   if (e == cudaSuccess) e = cudaMalloc(&S->d_list, max_slots * sizeof(int));
   if (e == cudaSuccess) {
     std::memset(S->h_state, 0, max_slots * sizeof(SysState));
@@ -438,15 +420,14 @@ rpcg_status rpcg_server_create(rpcg_server_t* out, size_t hbm_budget_bytes, int3
     return sm_count() * o;
   };
   if (e == cudaSuccess) {
-    cudaFuncSetAttribute((const void*)k_b_setup<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)b_smem<RPCG_EXBLAS>(3));
-    cudaFuncSetAttribute((const void*)k_b_pass_a<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)b_smem<RPCG_EXBLAS>(1));
-    cudaFuncSetAttribute((const void*)k_b_pass_b<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)b_smem<RPCG_EXBLAS>(2));
-    S->grid_setup = occ((const void*)k_b_setup<RPCG_EXBLAS, B>, b_smem<RPCG_EXBLAS>(3));
-    S->grid_a = occ((const void*)k_b_pass_a<RPCG_EXBLAS, B>, b_smem<RPCG_EXBLAS>(1));
-    S->grid_b = occ((const void*)k_b_pass_b<RPCG_EXBLAS, B>, b_smem<RPCG_EXBLAS>(2));
+    const size_t sm1 = b_smem<RPCG_EXBLAS>(1, max_slots), sm2 = b_smem<RPCG_EXBLAS>(2, max_slots),
+                 sm3 = b_smem<RPCG_EXBLAS>(3, max_slots);
+    cudaFuncSetAttribute((const void*)k_b_setup<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
+    cudaFuncSetAttribute((const void*)k_b_pass_a<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm1);
+    cudaFuncSetAttribute((const void*)k_b_pass_b<RPCG_EXBLAS, B>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm2);
+    S->grid_setup = occ((const void*)k_b_setup<RPCG_EXBLAS, B>, sm3);
+    S->grid_a = occ((const void*)k_b_pass_a<RPCG_EXBLAS, B>, sm1);
+    S->grid_b = occ((const void*)k_b_pass_b<RPCG_EXBLAS, B>, sm2);
     S->grid_c = occ((const void*)k_b_pass_c<B>, 0);
     S->grid_q = occ((const void*)k_b_inv_q, 0);
     e = cudaGetLastError();
@@ -554,12 +535,11 @@ rpcg_status rpcg_server_destroy(rpcg_server_t S) {
   cudaFreeHost(S->h_state);
   cudaFree(S->d_red);
   cudaFree(S->d_head);
-  cudaFree(S->d_units);
-  cudaFree(S->d_setup_units);
-  cudaFree(S->d_unit_count);
-  cudaFree(S->d_counts);
-  cudaFreeHost(S->h_counts);
-  cudaFree(S->d_partials);
+  cudaFree(S->d_aprefix);
+  cudaFree(S->d_sprefix);
+  cudaFreeHost(S->h_sprefix);
+  cudaFree(S->d_nunits);
+  cudaFreeHost(S->h_nunits);
   cudaFree(S->d_list);
   if (S->stream) cudaStreamDestroy(S->stream);
   delete S;

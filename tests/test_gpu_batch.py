@@ -57,7 +57,7 @@ def test_batch_bit_identical_to_solo(rpcg, cuda, tile):
         assert np.array_equal(bits(xs[i].cpu().numpy()), bits(x)), i
     if tile == 0:
         blk, tl = B.tuned()
-        assert blk in (128, 256) and tl in (2048, 8192, 32768)
+        assert blk in (128, 256) and tl in (1024, 4096, 16384)
     B.close()
 
 
@@ -117,3 +117,45 @@ def test_batch_rejects_duplicates_and_fpe(rpcg, cuda):
     x = torch.zeros(A.n, dtype=torch.float64, device=cuda)
     with pytest.raises(rpcg.RpcgError):
         B.solve([_dev(synth.rhs_uniform(A.n, 2), cuda)], [x], variant="fpe")
+
+
+@pytest.mark.parametrize("variant", ["exblas", "plain"])
+def test_batch_profiled_matches_graph(rpcg, cuda, variant):
+    """The pass-by-pass form launches the same kernels in the same order:
+    the same bits as the graph, one launch of A, B and C per iteration of the
+    longest-running system, one list launch more."""
+    import torch
+    mats, rhs = _systems()
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    bs = [_dev(b, cuda) for b in rhs]
+    B = rpcg.Batch(Ms)
+    xg = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    rg = B.solve(bs, xg, variant=variant, tol=1e-10, max_iter=3000, tile=64, block=128)
+    xp = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    rp, ms, nl = B.solve_profiled(bs, xp, variant=variant, tol=1e-10, max_iter=3000, tile=64, block=128)
+    for i in range(len(mats)):
+        assert rg[i]["iterations"] == rp[i]["iterations"]
+        assert bits([rg[i]["relres"]])[0] == bits([rp[i]["relres"]])[0]
+        assert np.array_equal(bits(xg[i].cpu().numpy()), bits(xp[i].cpu().numpy())), i
+    most = max(r["iterations"] for r in rg)
+    assert nl == {"setup": 3, "A": most, "B": most, "C": most, "list": most + 1}
+    assert all(v >= 0.0 for v in ms.values()) and ms["A"] > 0.0
+
+
+def test_batch_more_systems_than_shared_prefix(rpcg, cuda, oracle_lib):
+    """1100 systems: the unit prefix no longer fits the kernels' shared-memory
+    copy and is searched in global memory; every system still matches the
+    oracle bit for bit."""
+    import torch
+    mats, rhs = [], []
+    for k in range(1100):
+        A, _ = synth.diffusion7(1 + k % 3, SEED + 7 * k)
+        mats.append(A)
+        rhs.append(synth.rhs_uniform(A.n, SEED + 7 * k + 1))
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    res = rpcg.Batch(Ms).solve([_dev(b, cuda) for b in rhs], xs, tol=1e-12, max_iter=100, tile=8, block=128)
+    for i in range(0, 1100, 7):
+        ref = oracle_lib.pcg(mats[i], rhs[i], variant=oracle_lib.EXACT, tol=1e-12, max_iter=100)
+        assert res[i]["iterations"] == ref["iterations"] and res[i]["status"] == ref["status"], i
+        assert np.array_equal(bits(xs[i].cpu().numpy()), bits(ref["x"])), i
