@@ -209,10 +209,14 @@ rpcg_status rpcg_dot_plain(int64_t n, const double *a, const double *b, double *
  * tau = <r,r>; d = fma(RN(beta / beta'), d, z).  Set-up: inv = RN(1/diag),
  * r0 = RN(b - A x0), z0 = inv .* r0, d0 = z0, beta0 = <z0,r0>,
  * tau0 = <r0,r0>, ||b|| = RN(sqrt(<b,b>)).  The loop runs on the device
- * (a CUDA graph with a conditional while node) while relres >= tol and
- * iterations < max_iter.  With RPCG_EXBLAS, and RPCG_FPE with
- * fpe_strict = 0, every iterate, residual and the iteration count are
- * bit-identical for every launch shape.  b = 0 gives x = 0, 0 iterations.
+ * while relres >= tol and iterations < max_iter: as a CUDA graph of
+ * grid-wide passes with a conditional while node, or, for systems of up to
+ * 16384 rows whose slabs fit shared memory (plain and exblas variants, o->block
+ * and o->grid 0), as one launch of a thread-block cluster of up to 16 CTAs
+ * that keeps the matrix and vectors in shared memory (rpcg_solve_path).
+ * With RPCG_EXBLAS, and RPCG_FPE with fpe_strict = 0, every iterate,
+ * residual and the iteration count are bit-identical for every launch shape
+ * and on both paths.  b = 0 gives x = 0, 0 iterations.
  * Returns res->status.
  */
 rpcg_status rpcg_solve(rpcg_matrix_t A, const double *b, double *x, int32_t v, const rpcg_opts *o, rpcg_result *res,
@@ -229,6 +233,14 @@ rpcg_status rpcg_solve(rpcg_matrix_t A, const double *b, double *x, int32_t v, c
  */
 rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double *b, double *x, int32_t v, const rpcg_opts *o,
                                 rpcg_result *res, float *pass_ms, int32_t *launches, void *stream);
+
+/*
+ * rpcg_solve_path -- which path rpcg_solve takes for (A, v, o): *path = 1
+ * for the cluster-resident launch, 0 for the graph of grid-wide passes.
+ * (If the cluster cannot be made resident on this GPU, the first solve
+ * finds out and every later call answers 0.)  No GPU work.
+ */
+rpcg_status rpcg_solve_path(rpcg_matrix_t A, int32_t v, const rpcg_opts *o, int32_t *path);
 
 /*
  * rpcg_solve_host -- rpcg_solve with b and x in host memory: b and x0 are

@@ -27,7 +27,7 @@ VARIANTS = {"plain": PLAIN, "exblas": EXBLAS, "fpe": FPE}
 EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
-    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
+    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_solve_path", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
     "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_solve_profiled", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
     "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_eft_twosum",
     "rpcg_eft_twoprod",
@@ -243,6 +243,15 @@ class Matrix:
         if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
             _check(st, "rpcg_solve")
         return r.as_dict()
+
+    def solve_path(self, variant="exblas", **opts) -> str:
+        """Which path rpcg_solve takes: "cluster" (one cluster-resident launch)
+        or "graph" (grid-wide passes in a CUDA graph)."""
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o = make_opts(**opts)
+        p = ctypes.c_int32()
+        _check(lib().rpcg_solve_path(self._h, v, ctypes.byref(o), ctypes.byref(p)), "rpcg_solve_path")
+        return "cluster" if p.value == 1 else "graph"
 
     def solve_profiled(self, b, x, variant="exblas", stream=None, **opts) -> dict:
         """rpcg_solve_profiled: the result plus per-pass event times (ms) and launch counts."""

@@ -167,6 +167,7 @@ struct UnitSmem {
   long long dig[kNDig];
   uint32_t D[kNDig];
   double value[3];
+  int range[2];
   int base;
   bool last;
 };
@@ -270,9 +271,8 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         if constexpr (V == RPCG_EXBLAS) {
 #pragma unroll
           for (int j = 0; j < NACC; j++) {
-            for (int k = threadIdx.x; k < kNDig; k += BLOCK) us->dig[k] = (long long)atomicExch(&R->digits[j][k], 0ull);
-            __syncthreads();
-            if (threadIdx.x == 0) us->value[j] = round_digits(us->dig, us->D);
+            const double v = take_and_round(R->digits[j], us->dig, us->D, us->range);
+            if (threadIdx.x == 0) us->value[j] = v;
             __syncthreads();
           }
           if (threadIdx.x == 0) {

@@ -204,26 +204,41 @@ __device__ __forceinline__ void smem_acc_zero(unsigned long long* sacc, int nacc
 // Normalise the carries of kNDig signed digits and round the value
 // sum_k dig[k] 2^(32k + kE0) once to the nearest binary64, ties to even,
 // with gradual underflow and overflow to +-inf.  An exact zero gives +0.
-// Runs on one thread; D is kNDig words of scratch (shared memory).
-static __device__ __noinline__ double round_digits(const long long* dig, uint32_t* D) {
+// dig[k] must be zero outside [lo, hi] (lo > hi: every digit is zero).
+// Runs on one thread; D is kNDig words of scratch (shared memory), of which
+// only [lo, hi + 1] is written.
+//
+// Below lo every normalised digit is 0.  After digit hi the carry is
+// below 2^31 in magnitude, so digit hi + 1 takes it and every digit above
+// is the sign extension (0, or all ones for a negative value).  The
+// two's-complement negation of a negative value sends its +1 through the
+// zero digits below lo and stops at lo (that digit is non-zero), so the
+// magnitude lives in [lo, hi + 1] as well.
+static __device__ __noinline__ double round_digits_range(const long long* dig, uint32_t* D, int lo, int hi) {
+  if (lo > hi) return 0.0;
+  const int top = hi + 1 < kNDig ? hi + 1 : kNDig - 1;
   long long c = 0;
-  for (int k = 0; k < kNDig; k++) {
+  for (int k = lo; k <= top; k++) {
     const long long v = dig[k] + c;  // |dig| < 2^62, |c| < 2^31: no overflow
     D[k] = (uint32_t)v;
     c = v >> 32;  // arithmetic shift: floor division by 2^32
   }
-  const bool negative = c < 0;  // the top digits are all-ones for a negative value
+  const bool negative = c < 0;
   if (negative) {
     unsigned long long carry = 1;
-    for (int k = 0; k < kNDig; k++) {
+    for (int k = lo; k <= top; k++) {
       const unsigned long long t = (unsigned long long)(~D[k]) + carry;
       D[k] = (uint32_t)t;
       carry = t >> 32;
     }
   }
+  auto digit = [&](int k) -> uint32_t { return (k >= lo && k <= top) ? D[k] : 0u; };
   int kt = -1;
-  for (int k = kNDig - 1; k >= 0; k--) {
-    if (D[k]) { kt = k; break; }
+  for (int k = top; k >= lo; k--) {
+    if (D[k]) {
+      kt = k;
+      break;
+    }
   }
   if (kt < 0) return 0.0;
   const int t = 32 * kt + 31 - __clz(D[kt]);  // index of the leading bit
@@ -231,16 +246,16 @@ static __device__ __noinline__ double round_digits(const long long* dig, uint32_
   if (lsb < kSubLsb) lsb = kSubLsb;
   // 64 bits starting at lsb
   const int wi = lsb >> 5, bi = lsb & 31;
-  const unsigned long long lo = (unsigned long long)D[wi] | ((unsigned long long)(wi + 1 < kNDig ? D[wi + 1] : 0u) << 32);
-  const unsigned long long hi = (wi + 2 < kNDig) ? D[wi + 2] : 0u;
-  unsigned long long mant = bi ? ((lo >> bi) | (hi << (64 - bi))) : lo;
+  const unsigned long long w_lo = (unsigned long long)digit(wi) | ((unsigned long long)digit(wi + 1) << 32);
+  const unsigned long long w_hi = digit(wi + 2);
+  unsigned long long mant = bi ? ((w_lo >> bi) | (w_hi << (64 - bi))) : w_lo;
   const int nbits = t - lsb + 1;  // 1 .. 53
   mant &= (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
   // round bit and sticky bits below it
   const int rb_i = lsb - 1;
-  const uint32_t rbit = (D[rb_i >> 5] >> (rb_i & 31)) & 1u;
-  bool sticky = (D[rb_i >> 5] & ((1u << (rb_i & 31)) - 1u)) != 0u;
-  for (int k = (rb_i >> 5) - 1; k >= 0 && !sticky; k--) sticky = D[k] != 0u;
+  const uint32_t rbit = (digit(rb_i >> 5) >> (rb_i & 31)) & 1u;
+  bool sticky = (digit(rb_i >> 5) & ((1u << (rb_i & 31)) - 1u)) != 0u;
+  for (int k = (rb_i >> 5) - 1; k >= lo && !sticky; k--) sticky = D[k] != 0u;
   if (rbit && (sticky || (mant & 1ull))) mant += 1ull;
   if (mant == (1ull << 53)) {
     mant >>= 1;
@@ -256,6 +271,40 @@ static __device__ __noinline__ double round_digits(const long long* dig, uint32_
   }
   if (negative) bits |= 0x8000000000000000ull;
   return __longlong_as_double((long long)bits);
+}
+
+// round_digits_range over the non-zero digits of dig (found by a scan).
+static __device__ __noinline__ double round_digits(const long long* dig, uint32_t* D) {
+  int lo = kNDig, hi = -1;
+  for (int k = 0; k < kNDig; k++) {
+    if (dig[k]) {
+      lo = k < lo ? k : lo;
+      hi = k;
+    }
+  }
+  return round_digits_range(dig, D, lo, hi);
+}
+
+// Block-parallel form: every thread of the block calls it; the digits are
+// taken (and zeroed) from the global accumulator g into dig (shared), the
+// non-zero range is found with shared atomics, and thread 0 returns the
+// rounded value (the others return 0).  range is two ints of shared scratch.
+__device__ __forceinline__ double take_and_round(unsigned long long* g, long long* dig, uint32_t* D, int* range) {
+  if (threadIdx.x == 0) {
+    range[0] = kNDig;
+    range[1] = -1;
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < kNDig; k += blockDim.x) {
+    const long long v = (long long)atomicExch(&g[k], 0ull);
+    dig[k] = v;
+    if (v) {
+      atomicMin(&range[0], k);
+      atomicMax(&range[1], k);
+    }
+  }
+  __syncthreads();
+  return threadIdx.x == 0 ? round_digits_range(dig, D, range[0], range[1]) : 0.0;
 }
 
 // ------------------------------------------------------------------ EFTs and FPEs

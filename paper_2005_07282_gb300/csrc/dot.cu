@@ -103,11 +103,11 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
   __syncthreads();
   smem_to_global(sacc, ws->digits);
   if (is_last_block(&ws->counter)) {
-    for (int k = threadIdx.x; k < kNDig; k += BLOCK) sdig[k] = (long long)atomicExch(&ws->digits[k], 0ull);
-    __syncthreads();
+    __shared__ int srange[2];
+    const double v = take_and_round(ws->digits, sdig, sD, srange);
     if (threadIdx.x == 0) {
       const unsigned int f = atomicExch(&ws->flags, 0u);
-      *out = (f & 1u) ? __longlong_as_double(0x7FF8000000000000ll) : round_digits(sdig, sD);
+      *out = (f & 1u) ? __longlong_as_double(0x7FF8000000000000ll) : v;
       ws->counter = 0;
     }
   }

@@ -53,6 +53,7 @@ struct FinalScratch {  // shared memory of the CTA and grid reductions
   double value[3];
   int lost[3];
   int slost;
+  int range[2];
   bool last;
 };
 
@@ -183,9 +184,8 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
   __threadfence();
   if constexpr (V == RPCG_EXBLAS) {
     for (int j = 0; j < NACC; j++) {
-      for (int k = threadIdx.x; k < kNDig; k += BLOCK) fs->dig[k] = (long long)atomicExch(&ws->digits[j][k], 0ull);
-      __syncthreads();
-      if (threadIdx.x == 0) fs->value[j] = round_digits(fs->dig, fs->D);
+      const double v = take_and_round(ws->digits[j], fs->dig, fs->D, fs->range);
+      if (threadIdx.x == 0) fs->value[j] = v;
       __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -1037,6 +1037,7 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
   A->m.sptr = A->sptr;
   A->m.col = A->col;
   A->m.val = A->val;
+  small_plan(A, hsptr.data(), n);
   *A_out = A;
   return RPCG_OK;
 }
@@ -1099,13 +1100,20 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
     return RPCG_OK;
   }
   const bool eager = pass_ms != nullptr;
+  // small systems with the default launch shape: one cluster-resident launch
+  bool small = false;
+  if (!eager && opt.block == 0 && opt.grid == 0) {
+    rpcg_status st = small_solve(A, b, x, v, opt, s, &small);
+    if (st != RPCG_OK) return st;
+  }
   cudaGraphExec_t exec = nullptr;
-  if (!eager) {
+  if (!eager && !small) {
     rpcg_status st = get_graph(A, v, block, opt.grid, &exec);
     if (st != RPCG_OK) return st;
     RPCG_CUDA_TRY(set_x0(A, A->x0_nodes[GraphKey{v, block, opt.grid}], exec, x));
   }
   SolveArgs* ha = A->h_args;
+  if (!small) {
   ha->b = b;
   ha->x = x;
   ha->history = opt.history;
@@ -1130,6 +1138,7 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
     if (st != RPCG_OK) return st;
   } else {
     RPCG_CUDA_TRY(cudaGraphLaunch(exec, s));
+  }
   }
   RPCG_CUDA_TRY(cudaMemcpyAsync(A->h_state, A->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   RPCG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1172,6 +1181,16 @@ rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double* b, double* x, int
     if (launches) launches[i] = 0;
   }
   return solve_impl(A, b, x, v, o, res, (cudaStream_t)stream, pass_ms, launches);
+}
+
+rpcg_status rpcg_solve_path(rpcg_matrix_t A, int32_t v, const rpcg_opts* o, int32_t* path) {
+  clear_error();
+  RPCG_CHECK_ARG(A != nullptr && path != nullptr, "A or path is NULL");
+  rpcg_opts opt;
+  if (o) opt = *o;
+  else rpcg_opts_default(&opt);
+  *path = small_path(A, v, opt);
+  return RPCG_OK;
 }
 
 rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double* b_host, double* x_host, int32_t v, const rpcg_opts* o,

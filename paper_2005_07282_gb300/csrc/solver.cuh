@@ -8,6 +8,7 @@
 #include <tuple>
 
 #include "device.cuh"
+#include "small.h"
 #include "rpcg.h"
 
 namespace rpcg {
@@ -127,6 +128,7 @@ struct rpcg_matrix_s {
   std::map<rpcg::GraphKey, cudaGraphExec_t> graphs;
   std::map<rpcg::GraphKey, cudaGraph_t> graph_defs;
   std::map<rpcg::GraphKey, cudaGraphNode_t> x0_nodes;
+  rpcg::SmallPlan small;  // the cluster-resident path for small systems
   int device = 0;
 };
 
