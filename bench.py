@@ -107,6 +107,45 @@ def iter_bytes(n, nnz):
     return 12 * nnz + 4 * (n + 1) + 88 * n
 
 
+def l2_note(n, nnz):
+    """How the timed inputs relate to the 129 MB L2 (the timing rule)."""
+    csr = 12 * nnz + 4 * (n + 1)
+    if csr > (129 << 20):
+        return f"inputs larger than L2 (CSR {csr / 1e9:.2f} GB streamed every iteration)"
+    return (f"inputs fit in L2 (CSR {csr / 1e6:.2f} MB): a latency-bound workload, timed warm as a solver "
+            "sees it between iterations")
+
+
+def small_system_rates(P, dev, stream, steps=20):
+    """7-point Poisson 16^3 (4096 rows), b = A x_true, tol 1e-8: iterations/s
+    of complete solves for each variant, and the path rpcg_solve takes."""
+    import torch
+    A, xt = workload(16, 7, 0, 0)
+    M = P.Matrix.from_csr(A)
+    b = M.spmv(torch.from_numpy(xt).to(dev))
+    x = torch.zeros(A.n, dtype=torch.float64, device=dev)
+    out = {}
+    for v, k in (("exblas", steps), ("plain", steps), ("fpe", 3)):
+        for _ in range(3):
+            x.zero_()
+            r = M.solve(b, x, variant=v, tol=1e-8, max_iter=1000)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        it = 0
+        e0.record(stream)
+        for _ in range(k):
+            x.zero_()
+            r = M.solve(b, x, variant=v, tol=1e-8, max_iter=1000)
+            it += r["iterations"]
+        e1.record(stream)
+        torch.cuda.synchronize()
+        out[v] = {"iters_per_s": it / (e0.elapsed_time(e1) / 1e3), "iterations": r["iterations"],
+                  "status": r["status"], "path": M.solve_path(v)}
+    out["overhead_exblas_vs_plain"] = out["plain"]["iters_per_s"] / out["exblas"]["iters_per_s"]
+    out["workload"] = "poisson7_16 (n 4096, nnz 27136), b = A x_true, tol 1e-8, complete solves from x0 = 0"
+    return out
+
+
 def reduce_over_ranks(v, op, device):
     """Max or sum of a scalar over the ranks of the default process group
     (identity without one).  Timings take the max, work counts the sum."""
@@ -273,7 +312,10 @@ def gpu_arm(args, rank, world, local_rank):
     ms_max = max_over_ranks(ms)
     all_iters = sum_over_ranks(total_iters)
     value = all_iters / (ms_max / 1e3)
-    launches = args.steps * (4 + 3 * iters_per_solve)
+    path = "graph" if args.eager else M.solve_path(args.variant)
+    # our kernels per timed solve: one cluster launch, or the graph's set-up
+    # kernels plus passes A, B, C per iteration
+    launches = args.steps * (1 if path == "cluster" else 4 + 3 * iters_per_solve)
 
     extras = {}
     cpu = None
@@ -365,6 +407,9 @@ def gpu_arm(args, rank, world, local_rank):
         extras["exact_dot"] = {"n": nd, "gbs": gbs, "frac": gbs / peak, "ms": dms, "plain_dot_gbs": pgbs,
                                "inputs": "U[-1,1] pairs, 2^24 draw tiled 16x (4.3 GB, larger than L2)"}
         del da, db
+        # the small-system configuration (7-point 16^3, tol 1e-8): every variant
+        if not (args.stencil == 7 and args.side == 16 and not args.band):
+            extras["small_system"] = small_system_rates(P, dev, stream)
         # end to end through the host-buffer ABI: create from pinned host CSR, solve_host, destroy
         h_rowptr = torch.from_numpy(A.rowptr).pin_memory()
         h_col = torch.from_numpy(A.col).pin_memory()
@@ -400,9 +445,11 @@ def gpu_arm(args, rank, world, local_rank):
                 "config": {"workload": wl_name(args) + " " + args.variant, "n": n, "nnz": nnz, "tol": args.tol,
                            "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
                            "solve_status": status, "step": "one complete solve from x0 = 0",
-                           "l2": "inputs larger than L2 (CSR 5.46 GB streamed every iteration)",
+                           "l2": l2_note(n, nnz),
                            "parallelism": f"replicas x{world}",
-                           "launch": "eager (kernel by kernel)" if args.eager else "CUDA graph, device-side loop"},
+                           "launch": "eager (kernel by kernel)" if args.eager else
+                           ("one cluster-resident launch per solve" if path == "cluster" else
+                            "CUDA graph, device-side loop")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, **extras}
         print(json.dumps(line), flush=True)

@@ -185,9 +185,10 @@ __host__ __device__ constexpr size_t b_smem(int nacc, int count) {
 // Process the listed units of `prefix`, taking chunks from *work.
 // row_fn(sys, row, dep) deposits dep(j, a, b) into dot j; fin_fn(sys, values)
 // runs in thread 0 of the CTA that completes a system.
-template <int V, int NACC, int BLOCK, class PfFn, class RowFn, class FinFn>
+template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn>
 __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restrict__ prefix, unsigned int* work,
-                                          unsigned char* smem, PfFn pf_fn, RowFn row_fn, FinFn fin_fn) {
+                                          unsigned char* smem, CtxFn ctx_fn, PfFn pf_fn, RowFn row_fn,
+                                          FinFn fin_fn) {
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem);
   UnitSmem* us = reinterpret_cast<UnitSmem*>(smem + (V == RPCG_EXBLAS ? NACC * kNDig * kCopies * 8 : 0));
   const int copy = threadIdx.x & (kCopies - 1);
@@ -215,6 +216,10 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
       const int k0 = a - sp[s], k1 = k0 + (run_end - a);  // units [k0, k1) of system s
       const int n = B.sys[s].m.n;
       SysRed* R = B.red + s;
+      // what the rows of this run need (pointers, scalars) in registers: the
+      // row stores could alias the system table, so reading it per row would
+      // reload it every time
+      const auto ctx = ctx_fn(s);
       if constexpr (V == RPCG_EXBLAS) {
         Window win[NACC];
         bool bad = false;
@@ -225,8 +230,8 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         const int r0 = k0 * B.tile, r1 = min(n, k1 * B.tile);
         for (int row = r0 + threadIdx.x; row < r1; row += BLOCK) {
           const int ahead = row + kPfSteps * BLOCK;
-          if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(s, ahead, r1);
-          row_fn(s, row, [&](int j, double x, double y) {
+          if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(ctx, ahead);
+          row_fn(ctx, row, [&](int j, double x, double y) {
             const ExactProd e = exact_product(x, y);
             bad |= e.bad;
             exact_deposit(win[j], sacc + j * kNDig * kCopies, copy, e);
@@ -247,8 +252,8 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
           const int r0 = k * B.tile, r1 = min(n, (k + 1) * B.tile);
           for (int row = r0 + threadIdx.x; row < r1; row += BLOCK) {
             const int ahead = row + kPfSteps * BLOCK;
-            if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(s, ahead, r1);
-            row_fn(s, row, [&](int j, double x, double y) { acc[j] = __fma_rn(x, y, acc[j]); });
+            if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(ctx, ahead);
+            row_fn(ctx, row, [&](int j, double x, double y) { acc[j] = __fma_rn(x, y, acc[j]); });
           }
 #pragma unroll
           for (int j = 0; j < NACC; j++) {
@@ -301,6 +306,23 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
 }
 
 // ------------------------------------------------------------------ kernels
+
+// Per-run contexts of the reducing passes.
+struct PassACtx {
+  MatDev m;
+  const double* __restrict__ d;
+  double* __restrict__ w;
+};
+
+struct PassBCtx {
+  double* __restrict__ x;
+  double* __restrict__ r;
+  const double* __restrict__ d;
+  const double* __restrict__ w;
+  const double* __restrict__ inv;
+  double rho;
+  bool stopped;
+};
 
 // Reset the states of every system with rows, list their units, clear the
 // work counters (one block).
@@ -380,9 +402,8 @@ template <int V, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_b_setup(BatchDesc B, const int* __restrict__ prefix) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 3, BLOCK>(
-      B, prefix, &B.head->work[kWorkSetup], smem, [](int, int, int) {},
-      [&](int s, int i, auto dep) {
-        const SysDev& S = B.sys[s];
+      B, prefix, &B.head->work[kWorkSetup], smem, [&](int s) { return B.sys[s]; }, [](const SysDev&, int) {},
+      [&](const SysDev& S, int i, auto dep) {
         const double bi = S.b[i];
         const double ri = __dsub_rn(bi, S.w[i]);
         const double zi = __dmul_rn(S.inv[i], ri);
@@ -435,12 +456,15 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_a(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 1, BLOCK>(
       B, B.aprefix, &B.head->work[kWorkA], smem,
-      [&](int s, int i, int) { l2_prefetch_slice(B.sys[s].m, i); },
-      [&](int s, int i, auto dep) {
+      [&](int s) {
         const SysDev& S = B.sys[s];
-        const double v = sell_row(S.m, i, S.d);
-        S.w[i] = v;
-        dep(0, __ldg(S.d + i), v);
+        return PassACtx{S.m, S.d, S.w};
+      },
+      [](const PassACtx& c, int i) { l2_prefetch_slice(c.m, i); },
+      [&](const PassACtx& c, int i, auto dep) {
+        const double v = sell_row(c.m, i, c.d);
+        c.w[i] = v;
+        dep(0, __ldg(c.d + i), v);
       },
       [&](int s, const double* v) {
         SysState* t = B.st + s;
@@ -464,18 +488,21 @@ template <int V, int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 2, BLOCK>(
-      B, B.aprefix, &B.head->work[kWorkB], smem, [](int, int, int) {},
-      [&](int s, int i, auto dep) {
+      B, B.aprefix, &B.head->work[kWorkB], smem,
+      [&](int s) {
         const SysDev& S = B.sys[s];
         const SysState& t = B.st[s];
-        if (t.status != 0) return;  // stopped in pass A of this iteration
-        const double rho = t.rho;
-        const double di = S.d[i], wi = S.w[i];
-        const double xi = __fma_rn(rho, di, S.x[i]);
-        const double ri = __fma_rn(-rho, wi, S.r[i]);
-        const double zi = __dmul_rn(S.inv[i], ri);
-        S.x[i] = xi;
-        S.r[i] = ri;
+        return PassBCtx{S.x, S.r, S.d, S.w, S.inv, t.rho, t.status != 0};
+      },
+      [](const PassBCtx&, int) {},
+      [&](const PassBCtx& c, int i, auto dep) {
+        if (c.stopped) return;  // stopped in pass A of this iteration
+        const double di = c.d[i], wi = c.w[i];
+        const double xi = __fma_rn(c.rho, di, c.x[i]);
+        const double ri = __fma_rn(-c.rho, wi, c.r[i]);
+        const double zi = __dmul_rn(c.inv[i], ri);
+        c.x[i] = xi;
+        c.r[i] = ri;
         dep(0, zi, ri);
         dep(1, ri, ri);
       },

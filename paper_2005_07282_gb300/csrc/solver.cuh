@@ -59,10 +59,9 @@ __device__ __forceinline__ long long sell_index(const MatDev& m, int row, int k)
 // slices.  The matrix stream is read with coalesced streaming loads; the
 // gathers x[col] go through L1/L2 (stencil locality).  The loads of the
 // next 8 entries are issued before the FMAs of the current 8.
-__device__ __forceinline__ double sell_row(const MatDev& m, int row, const double* __restrict__ x) {
+// The row whose entry k sits at base + 32 k, of length len.
+__device__ __forceinline__ double sell_row_at(const MatDev& m, long long base, int len, const double* __restrict__ x) {
   constexpr int U = 8;
-  const int len = __ldg(m.rowptr + row + 1) - __ldg(m.rowptr + row);
-  const long long base = sell_index(m, row, 0);
   const double* __restrict__ vp = m.val + base;
   const int* __restrict__ cp = m.col + base;
   double acc = 0.0;
@@ -98,6 +97,11 @@ __device__ __forceinline__ double sell_row(const MatDev& m, int row, const doubl
     }
   }
   return acc;
+}
+
+__device__ __forceinline__ double sell_row(const MatDev& m, int row, const double* __restrict__ x) {
+  const int len = __ldg(m.rowptr + row + 1) - __ldg(m.rowptr + row);
+  return sell_row_at(m, sell_index(m, row, 0), len, x);
 }
 
 struct GraphKey {
