@@ -90,7 +90,7 @@ def workload(side, stencil=27, band=0, band_n=0):
 # capture summarised in profiles/k_pass_a_p27_128.md (dram read + write of the
 # 128^3 case / its algorithmic bytes); the kernel streams every matrix entry
 # once, so the full-size launch's traffic is this ratio times its bytes.
-PASS_A_TRAFFIC_RATIO = 701.7 / 710.9
+PASS_A_TRAFFIC_RATIO = 701.9 / 710.9
 
 
 def wl_name(args):
