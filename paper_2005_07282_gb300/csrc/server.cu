@@ -34,7 +34,7 @@
 namespace rpcg {
 
 constexpr int kChunk = 16;          // iterations between scheduling decisions
-constexpr int kServeTile = 8192;    // rows per work unit
+constexpr int kServeTile = 1024;    // rows per work unit (the batch autotuner's choice on stencil systems)
 constexpr int kServeBlock = 128;
 
 static double now_us() {

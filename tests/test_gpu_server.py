@@ -54,7 +54,10 @@ def test_server_admits_work_while_others_run(rpcg, cuda):
     b_big = synth.rhs_uniform(big.n, 9)
     small = synth.poisson7(8)
     srv = rpcg.Server(hbm_budget_bytes=4 << 30, max_slots=8)
-    t_big = srv.submit(big, b_big, tol=1e-12, max_iter=2000)
+    # tol below what any iterate reaches: the big solve runs its 3000
+    # iterations (hundreds of ms), so it is still running when the short
+    # requests arrive however fast the passes are
+    t_big = srv.submit(big, b_big, tol=1e-30, max_iter=3000)
     time.sleep(0.02)
     t_small = [srv.submit(small, synth.rhs_uniform(small.n, 50 + k), tol=1e-8) for k in range(5)]
     done_order = []
