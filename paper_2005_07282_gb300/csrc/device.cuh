@@ -46,7 +46,8 @@ struct ExactProd {
   bool bad;  // a or b is Inf or NaN
 };
 
-__device__ __forceinline__ ExactProd exact_product(double a, double b) {
+// General form: every finite, zero, subnormal, infinite or NaN operand.
+__device__ __forceinline__ ExactProd exact_product_general(double a, double b) {
   // everything on 32-bit halves: exponent field, significand high part
   // with the hidden bit (normal numbers) or without it (subnormals, whose
   // exponent is that of field 1)
@@ -82,6 +83,45 @@ __device__ __forceinline__ ExactProd exact_product(double a, double b) {
   // a zero product (either significand zero) yields five zero words: adding
   // it anywhere changes nothing, so no separate test is needed on the fast path
   p.nz = !p.bad;
+  return p;
+}
+
+// Fast form for two normal operands (exponent field neither 0 nor all
+// ones), the case of every product in practice; others take the general
+// form (inlined: a call in the per-element loop costs more than it saves).
+// Same fields, fewer ALU instructions: the exponent sum comes from the two
+// exponent fields in place, with no subnormal clamps or hidden-bit selects.
+__device__ __forceinline__ ExactProd exact_product(double a, double b) {
+  const uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  const uint32_t bh = (uint32_t)__double2hiint(b), bl = (uint32_t)__double2loint(b);
+  const uint32_t fa = ah & 0x7ff00000u, fb = bh & 0x7ff00000u;
+  // field 0 wraps to 0xfff00000, field 0x7ff to 0x7fe00000: both outside the normal range
+  if ((fa - 0x00100000u) >= 0x7fe00000u || (fb - 0x00100000u) >= 0x7fe00000u) return exact_product_general(a, b);
+  ExactProd p;
+  p.bad = false;
+  p.nz = true;
+  const uint32_t mah = (ah & 0x000FFFFFu) | 0x00100000u;
+  const uint32_t mbh = (bh & 0x000FFFFFu) | 0x00100000u;
+  const int o = (int)((fa + fb) >> 20) - 2150 - kE0;  // fa + fb < 2^32
+  p.q = o >> 5;
+  const uint32_t r = (uint32_t)o & 31u;
+  const uint64_t p0 = (uint64_t)al * bl;
+  const uint64_t p1 = (uint64_t)al * mbh + (uint64_t)mah * bl;  // < 2^54
+  const uint64_t p2 = (uint64_t)mah * mbh;                      // < 2^42
+  const uint32_t v0 = (uint32_t)p0;
+  uint32_t v1, v2, v3;
+  asm("add.cc.u32 %0, %3, %4;\n\t"
+      "addc.cc.u32 %1, %5, %6;\n\t"
+      "addc.u32 %2, %7, 0;"
+      : "=r"(v1), "=r"(v2), "=r"(v3)
+      : "r"((uint32_t)(p0 >> 32)), "r"((uint32_t)p1), "r"((uint32_t)(p1 >> 32)), "r"((uint32_t)p2),
+        "r"((uint32_t)(p2 >> 32)));
+  p.w0 = v0 << r;
+  p.w1 = __funnelshift_l(v0, v1, r);
+  p.w2 = __funnelshift_l(v1, v2, r);
+  p.w3 = __funnelshift_l(v2, v3, r);
+  p.w4 = __funnelshift_l(v3, 0u, r);
+  p.neg = (uint32_t)((int32_t)(ah ^ bh) >> 31);
   return p;
 }
 

@@ -280,9 +280,29 @@ __global__ void __launch_bounds__(BLOCK) k_dot_plain(int64_t n, const double* __
   }
 }
 
-static int dot_grid(int64_t n, int per_thread, int cap) {
+// CTAs of k_dot_exact resident per SM on the current device (its 80
+// registers allow 3 CTAs of 256 threads; a grid of exactly that many leaves
+// no partial second wave).
+static int exact_resident() {
+  static int cache[64] = {0};
+  int dev = 0;
+  cudaGetDevice(&dev);
+  if (dev < 0 || dev >= 64) dev = 0;
+  if (!cache[dev]) {
+    int occ = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dot_exact<kDotBlock>, kDotBlock, 0) != cudaSuccess ||
+        occ < 1) {
+      cudaGetLastError();
+      occ = 4;
+    }
+    cache[dev] = occ;
+  }
+  return cache[dev];
+}
+
+static int dot_grid(int64_t n, int per_thread, int cap, int per_sm = 4) {
   int64_t want = (n + (int64_t)kDotBlock * per_thread - 1) / ((int64_t)kDotBlock * per_thread);
-  int64_t g = sm_count() * 4;
+  int64_t g = (int64_t)sm_count() * per_sm;
   if (want < g) g = want;
   if (g < 1) g = 1;
   if (g > cap) g = cap;
@@ -325,7 +345,7 @@ static rpcg_status dot_common(int kind, int64_t n, const double* a, const double
   cudaError_t e = cudaMemsetAsync(ws, 0, kDotScratchHeader, s);
   if (e == cudaSuccess) {
     if (kind == 0) {
-      k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
+      k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid, exact_resident()), kDotBlock, 0, s>>>(n, a, b, ws, out);
     } else if (kind == 1) {
       k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kFpeDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
     } else {
@@ -443,7 +463,7 @@ extern "C" rpcg_status rpcg_dot_exact_noalloc(int64_t n, const double* a, const 
   // the array keeps the previous call's contents: clear the part the kernel
   // expects to start at zero (accumulator digits, arrival counter, flags)
   RPCG_CUDA_TRY(cudaMemsetAsync(ws, 0, kDotScratchHeader, s));
-  k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
+  k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid, exact_resident()), kDotBlock, 0, s>>>(n, a, b, ws, out);
   RPCG_CUDA_TRY(cudaGetLastError());
   return RPCG_OK;
 }
