@@ -57,7 +57,21 @@ __device__ __forceinline__ void exact_step(Window& win, unsigned long long* sacc
   exact_deposit(win, sacc, copy, p);
 }
 
-template <int BLOCK>
+// The last CTA: normalise, round once, publish, leave the scratch clean.
+// Out of line so that its registers do not count against the main loop's.
+static __device__ __noinline__ void dot_exact_finish(DotScratch* ws, double* out, long long* sdig, uint32_t* sD) {
+  __shared__ int srange[2];
+  const double v = take_and_round(ws->digits, sdig, sD, srange);
+  if (threadIdx.x == 0) {
+    const unsigned int f = atomicExch(&ws->flags, 0u);
+    *out = (f & 1u) ? __longlong_as_double(0x7FF8000000000000ll) : v;
+    ws->counter = 0;
+  }
+}
+
+// ALIGNED: a and b start on 16-byte boundaries (pairs of elements are
+// loaded as double2); the host picks the instance.
+template <int BLOCK, bool ALIGNED>
 __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, DotScratch* ws, double* out) {
   __shared__ unsigned long long sacc[kNDig * kCopies];
@@ -71,7 +85,7 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
   bool bad = false;
   const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * BLOCK;
-  if ((((uintptr_t)a | (uintptr_t)b) & 15) == 0) {
+  if constexpr (ALIGNED) {
     const double2* a2 = reinterpret_cast<const double2*>(a);
     const double2* b2 = reinterpret_cast<const double2*>(b);
     const int64_t n2 = n >> 1;
@@ -102,15 +116,7 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
   if (bad) atomicOr(&ws->flags, 1u);
   __syncthreads();
   smem_to_global(sacc, ws->digits);
-  if (is_last_block(&ws->counter)) {
-    __shared__ int srange[2];
-    const double v = take_and_round(ws->digits, sdig, sD, srange);
-    if (threadIdx.x == 0) {
-      const unsigned int f = atomicExch(&ws->flags, 0u);
-      *out = (f & 1u) ? __longlong_as_double(0x7FF8000000000000ll) : v;
-      ws->counter = 0;
-    }
-  }
+  if (is_last_block(&ws->counter)) dot_exact_finish(ws, out, sdig, sD);
 }
 
 // ------------------------------------------------------------------ FPE dot
@@ -280,9 +286,10 @@ __global__ void __launch_bounds__(BLOCK) k_dot_plain(int64_t n, const double* __
   }
 }
 
-// CTAs of k_dot_exact resident per SM on the current device (its 80
-// registers allow 3 CTAs of 256 threads; a grid of exactly that many leaves
-// no partial second wave).
+// CTAs of k_dot_exact resident per SM on the current device (3 of 256
+// threads at its 80 registers; a grid of exactly that many leaves no
+// partial second wave).  A 64-register cap (4 CTAs) spilled and measured
+// no faster.
 static int exact_resident() {
   static int cache[64] = {0};
   int dev = 0;
@@ -290,7 +297,7 @@ static int exact_resident() {
   if (dev < 0 || dev >= 64) dev = 0;
   if (!cache[dev]) {
     int occ = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dot_exact<kDotBlock>, kDotBlock, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_dot_exact<kDotBlock, true>, kDotBlock, 0) != cudaSuccess ||
         occ < 1) {
       cudaGetLastError();
       occ = 4;
@@ -307,6 +314,13 @@ static int dot_grid(int64_t n, int per_thread, int cap, int per_sm = 4) {
   if (g < 1) g = 1;
   if (g > cap) g = cap;
   return (int)g;
+}
+
+static void launch_dot_exact(int64_t n, const double* a, const double* b, DotScratch* ws, double* out,
+                             cudaStream_t s) {
+  const int g = dot_grid(n, 8, kDotMaxGrid, exact_resident());
+  if ((((uintptr_t)a | (uintptr_t)b) & 15) == 0) k_dot_exact<kDotBlock, true><<<g, kDotBlock, 0, s>>>(n, a, b, ws, out);
+  else k_dot_exact<kDotBlock, false><<<g, kDotBlock, 0, s>>>(n, a, b, ws, out);
 }
 
 }  // namespace rpcg
@@ -345,7 +359,7 @@ static rpcg_status dot_common(int kind, int64_t n, const double* a, const double
   cudaError_t e = cudaMemsetAsync(ws, 0, kDotScratchHeader, s);
   if (e == cudaSuccess) {
     if (kind == 0) {
-      k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid, exact_resident()), kDotBlock, 0, s>>>(n, a, b, ws, out);
+      launch_dot_exact(n, a, b, ws, out, s);
     } else if (kind == 1) {
       k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kFpeDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
     } else {
@@ -463,7 +477,7 @@ extern "C" rpcg_status rpcg_dot_exact_noalloc(int64_t n, const double* a, const 
   // the array keeps the previous call's contents: clear the part the kernel
   // expects to start at zero (accumulator digits, arrival counter, flags)
   RPCG_CUDA_TRY(cudaMemsetAsync(ws, 0, kDotScratchHeader, s));
-  k_dot_exact<kDotBlock><<<dot_grid(n, 8, kDotMaxGrid, exact_resident()), kDotBlock, 0, s>>>(n, a, b, ws, out);
+  launch_dot_exact(n, a, b, ws, out, s);
   RPCG_CUDA_TRY(cudaGetLastError());
   return RPCG_OK;
 }
