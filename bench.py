@@ -487,18 +487,6 @@ def dot_arm(args):
                       "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
 
 
-def batch_systems(count, seed):
-    """The batched workload: variable-coefficient 7-point diffusion systems on
-    s^3 grids, s uniform in [8, 64], b ~ U[-1, 1] per system."""
-    sides = synth.uniform_int(synth.stream_seed(seed, 50), count, 8, 64)
-    mats, rhs = [], []
-    for i, s in enumerate(sides.tolist()):
-        A, _ = synth.diffusion7(int(s), synth.stream_seed(seed, 1000 + i))
-        mats.append(A)
-        rhs.append(synth.rhs_uniform(A.n, synth.stream_seed(seed, 5000 + i)))
-    return mats, rhs
-
-
 def batch_arm(args):
     """--batch COUNT: one batched solve of COUNT systems per step (exblas,
     tol 1e-10), against solving the same systems one after the other."""
@@ -509,7 +497,7 @@ def batch_arm(args):
     B.build()
     dev = torch.device("cuda", 0)
     t0 = time.perf_counter()
-    mats, rhs = batch_systems(args.batch, synth.BASE_SEED + 3)
+    mats, rhs = synth.diffusion_batch(args.batch, synth.BASE_SEED + 3)
     gen_s = time.perf_counter() - t0
     Ms = [P.Matrix.from_csr(A) for A in mats]
     bs = [torch.from_numpy(b).to(dev) for b in rhs]

@@ -309,3 +309,17 @@ def poisson_rhs_xtrue(n: int, seed: int) -> np.ndarray:
 def rhs_uniform(n: int, seed: int) -> np.ndarray:
     """A right-hand side b ~ U[-1, 1] drawn directly."""
     return uniform_pm1(stream_seed(seed, 8), n)
+
+
+def diffusion_batch(count: int, seed: int) -> tuple[list, list]:
+    """The batched workload: `count` variable-coefficient 7-point diffusion
+    systems on s^3 grids with s uniform in [8, 64], b ~ U[-1, 1] per system.
+    Returns (list of CSR, list of right-hand sides)."""
+    sides = uniform_int(stream_seed(seed, 50), count, 8, 64)
+    mats, rhs = [], []
+    for i, s in enumerate(sides.tolist()):
+        A, _ = diffusion7(int(s), stream_seed(seed, 1000 + i))
+        mats.append(A)
+        rhs.append(rhs_uniform(A.n, stream_seed(seed, 5000 + i)))
+    return mats, rhs
+

@@ -77,3 +77,29 @@ def test_poisson27_256_full_solve_properties(rpcg, cuda, big_system):
     r3 = M.solve(db, x3, variant="fpe", tol=1e-8, max_iter=5000)
     assert r3["iterations"] == r1["iterations"]
     assert torch.equal(x1.view(torch.int64), x3.view(torch.int64))
+
+
+def test_batch_256_full_config(rpcg, cuda, oracle_lib):
+    """The batched configuration at its full size (256 diffusion systems,
+    s ~ U{8..64}, tol 1e-10), autotuned as bench.py runs it: every system
+    bit-identical to solving it alone, and sampled systems (the three
+    smallest and one of median size) bit-identical to the oracle."""
+    import torch
+    mats, rhs = synth.diffusion_batch(256, synth.BASE_SEED + 3)
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    bs = [torch.from_numpy(b).to(cuda) for b in rhs]
+    xs = [torch.zeros(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    res = rpcg.Batch(Ms).solve(bs, xs, variant="exblas", tol=1e-10, max_iter=5000)
+    assert all(r["status"] == 0 for r in res)
+    for i, (M, b) in enumerate(zip(Ms, bs)):
+        x = torch.zeros(M.n, dtype=torch.float64, device=cuda)
+        r = M.solve(b, x, variant="exblas", tol=1e-10, max_iter=5000)
+        assert r["iterations"] == res[i]["iterations"], i
+        assert bits([r["relres"]])[0] == bits([res[i]["relres"]])[0], i
+        assert torch.equal(x.view(torch.int64), xs[i].view(torch.int64)), i
+    order = sorted(range(len(mats)), key=lambda k: mats[k].n)
+    for i in order[:3] + [order[len(order) // 2]]:
+        ref = oracle_lib.pcg(mats[i], rhs[i], variant=oracle_lib.EXACT, tol=1e-10, max_iter=5000,
+                             nthreads=oracle_lib.default_threads())
+        assert ref["iterations"] == res[i]["iterations"], i
+        assert np.array_equal(bits(xs[i].cpu().numpy()), bits(ref["x"])), i
