@@ -16,6 +16,7 @@
 // finishes it.
 #pragma once
 #include <climits>
+#include <type_traits>
 
 #include "device.cuh"
 #include "solver.cuh"
@@ -185,10 +186,15 @@ __host__ __device__ constexpr size_t b_smem(int nacc, int count) {
 // Process the listed units of `prefix`, taking chunks from *work.
 // row_fn(sys, row, dep) deposits dep(j, a, b) into dot j; fin_fn(sys, values)
 // runs in thread 0 of the CTA that completes a system.
-template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn>
+// row2_fn(ctx, ra, rb, dep) does rows ra and rb together (both in range);
+// pass a null_row2 to process rows one at a time.
+struct NullRow2 {};
+
+template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn, class Row2Fn = NullRow2>
 __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restrict__ prefix, unsigned int* work,
                                           unsigned char* smem, CtxFn ctx_fn, PfFn pf_fn, RowFn row_fn,
-                                          FinFn fin_fn) {
+                                          FinFn fin_fn, Row2Fn row2_fn = NullRow2{}) {
+  constexpr bool kPair = !std::is_same<Row2Fn, NullRow2>::value;
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem);
   UnitSmem* us = reinterpret_cast<UnitSmem*>(smem + (V == RPCG_EXBLAS ? NACC * kNDig * kCopies * 8 : 0));
   const int copy = threadIdx.x & (kCopies - 1);
@@ -228,14 +234,20 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         smem_acc_zero(sacc, NACC);
         __syncthreads();
         const int r0 = k0 * B.tile, r1 = min(n, k1 * B.tile);
-        for (int row = r0 + threadIdx.x; row < r1; row += BLOCK) {
+        auto dep = [&](int j, double x, double y) {
+          const ExactProd e = exact_product(x, y);
+          bad |= e.bad;
+          exact_deposit(win[j], sacc + j * kNDig * kCopies, copy, e);
+        };
+        for (int row = r0 + threadIdx.x; row < r1; row += (kPair ? 2 : 1) * BLOCK) {
           const int ahead = row + kPfSteps * BLOCK;
           if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(ctx, ahead);
-          row_fn(ctx, row, [&](int j, double x, double y) {
-            const ExactProd e = exact_product(x, y);
-            bad |= e.bad;
-            exact_deposit(win[j], sacc + j * kNDig * kCopies, copy, e);
-          });
+          if constexpr (kPair) {
+            if (row + BLOCK < r1) row2_fn(ctx, row, row + BLOCK, dep);
+            else row_fn(ctx, row, dep);
+          } else {
+            row_fn(ctx, row, dep);
+          }
         }
 #pragma unroll
         for (int j = 0; j < NACC; j++) window_flush(win[j], sacc + j * kNDig * kCopies, copy);
@@ -250,10 +262,11 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
 #pragma unroll
           for (int j = 0; j < NACC; j++) acc[j] = 0.0;
           const int r0 = k * B.tile, r1 = min(n, (k + 1) * B.tile);
+          auto dep = [&](int j, double x, double y) { acc[j] = __fma_rn(x, y, acc[j]); };
           for (int row = r0 + threadIdx.x; row < r1; row += BLOCK) {
             const int ahead = row + kPfSteps * BLOCK;
             if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(ctx, ahead);
-            row_fn(ctx, row, [&](int j, double x, double y) { acc[j] = __fma_rn(x, y, acc[j]); });
+            row_fn(ctx, row, dep);
           }
 #pragma unroll
           for (int j = 0; j < NACC; j++) {
@@ -452,7 +465,7 @@ __global__ void __launch_bounds__(BLOCK) k_b_setup(BatchDesc B, const int* __res
 }
 
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_a(BatchDesc B) {
+__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_b_pass_a(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 1, BLOCK>(
       B, B.aprefix, &B.head->work[kWorkA], smem,
@@ -481,6 +494,14 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_a(BatchDesc B) {
         }
         t->beta_old = t->beta;
         t->rho = __ddiv_rn(t->beta, dw);
+      },
+      [&](const PassACtx& c, int ia, int ib, auto dep) {
+        double va, vb;
+        sell_rows2(c.m, ia, ib, c.d, va, vb);
+        c.w[ia] = va;
+        c.w[ib] = vb;
+        dep(0, __ldg(c.d + ia), va);
+        dep(0, __ldg(c.d + ib), vb);
       });
 }
 

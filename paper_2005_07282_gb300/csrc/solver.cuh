@@ -104,6 +104,48 @@ __device__ __forceinline__ double sell_row(const MatDev& m, int row, const doubl
   return sell_row_at(m, sell_index(m, row, 0), len, x);
 }
 
+// Two rows at once (ya = row ra of A x, yb = row rb): when both have at
+// most 8 entries, their loads are issued together, so a thread keeps two
+// rows' memory chains in flight with the registers sell_row spends on
+// prefetching a row's next 8 entries.  Longer rows take sell_row.  Each
+// row's fma chain is the one of sell_row.
+__device__ __forceinline__ void sell_rows2(const MatDev& m, int ra, int rb, const double* __restrict__ x, double& ya,
+                                           double& yb) {
+  constexpr int U = 8;
+  const int la = __ldg(m.rowptr + ra + 1) - __ldg(m.rowptr + ra);
+  const int lb = __ldg(m.rowptr + rb + 1) - __ldg(m.rowptr + rb);
+  if (la > U || lb > U) {
+    ya = sell_row(m, ra, x);
+    yb = sell_row(m, rb, x);
+    return;
+  }
+  const long long ba = sell_index(m, ra, 0), bb = sell_index(m, rb, 0);
+  double va[U], xa[U], vb[U], xb[U];
+#pragma unroll
+  for (int j = 0; j < U; j++) {
+    va[j] = 0.0;
+    xa[j] = 0.0;
+    vb[j] = 0.0;
+    xb[j] = 0.0;
+    if (j < la) {
+      va[j] = __ldcs(m.val + ba + 32 * j);
+      xa[j] = __ldg(x + __ldcs(m.col + ba + 32 * j));
+    }
+    if (j < lb) {
+      vb[j] = __ldcs(m.val + bb + 32 * j);
+      xb[j] = __ldg(x + __ldcs(m.col + bb + 32 * j));
+    }
+  }
+  double a = 0.0, b = 0.0;
+#pragma unroll
+  for (int j = 0; j < U; j++) {
+    if (j < la) a = __fma_rn(va[j], xa[j], a);
+    if (j < lb) b = __fma_rn(vb[j], xb[j], b);
+  }
+  ya = a;
+  yb = b;
+}
+
 struct GraphKey {
   int variant, block, grid;
   bool operator<(const GraphKey& o) const {
