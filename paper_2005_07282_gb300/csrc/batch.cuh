@@ -552,6 +552,22 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
         if (!((t->rel >= S.tol) && (t->iter < S.max_iter))) {
           t->active = 2;  // finished this iteration: pass C still updates d (unobservable), then it stops
         }
+      },
+      [&](const PassBCtx& c, int ia, int ib, auto dep) {
+        if (c.stopped) return;
+        // both rows' loads first, then the arithmetic of each row as in the single-row form
+        const double da = c.d[ia], wa = c.w[ia], xa0 = c.x[ia], ra0 = c.r[ia], va = c.inv[ia];
+        const double db = c.d[ib], wb = c.w[ib], xb0 = c.x[ib], rb0 = c.r[ib], vb = c.inv[ib];
+        const double xa = __fma_rn(c.rho, da, xa0), ra = __fma_rn(-c.rho, wa, ra0), za = __dmul_rn(va, ra);
+        const double xb = __fma_rn(c.rho, db, xb0), rb = __fma_rn(-c.rho, wb, rb0), zb = __dmul_rn(vb, rb);
+        c.x[ia] = xa;
+        c.r[ia] = ra;
+        c.x[ib] = xb;
+        c.r[ib] = rb;
+        dep(0, za, ra);
+        dep(1, ra, ra);
+        dep(0, zb, rb);
+        dep(1, rb, rb);
       });
 }
 
