@@ -313,6 +313,87 @@ static __device__ __noinline__ double round_digits_range(const long long* dig, u
   return __longlong_as_double((long long)bits);
 }
 
+// round_digits_range for the common case of at most kRegDigits digits in
+// [lo, min(hi + 1, kNDig - 1)]: the same steps on an unrolled register copy
+// (no shared-memory round trip per digit; digits are picked by compare and
+// select, so nothing is indexed dynamically).  Callers check the width.
+constexpr int kRegDigits = 8;
+
+__device__ __forceinline__ uint32_t reg_digit(const uint32_t (&D)[kRegDigits], int k) {
+  uint32_t v = 0u;
+#pragma unroll
+  for (int j = 0; j < kRegDigits; j++) v = (k == j) ? D[j] : v;
+  return v;
+}
+
+__device__ __forceinline__ double round_digits_reg(const long long* dig, int lo, int hi) {
+  if (lo > hi) return 0.0;
+  const int top = hi + 1 < kNDig ? hi + 1 : kNDig - 1;
+  const int cnt = top - lo + 1;  // <= kRegDigits
+  uint32_t D[kRegDigits];
+  long long c = 0;
+#pragma unroll
+  for (int k = 0; k < kRegDigits; k++) {
+    const long long v = (k < cnt ? dig[lo + k] : 0ll) + c;
+    D[k] = (uint32_t)v;
+    c = k < cnt ? (v >> 32) : c;
+  }
+  const bool negative = c < 0;
+  if (negative) {
+    unsigned long long carry = 1;
+#pragma unroll
+    for (int k = 0; k < kRegDigits; k++) {
+      const unsigned long long t = (unsigned long long)(~D[k]) + carry;
+      D[k] = (uint32_t)t;
+      carry = t >> 32;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kRegDigits; k++) D[k] = k < cnt ? D[k] : 0u;  // above top: zero once negated
+  int kt = -1;
+#pragma unroll
+  for (int k = 0; k < kRegDigits; k++) kt = D[k] ? k : kt;
+  if (kt < 0) return 0.0;
+  const int t = 32 * (lo + kt) + 31 - __clz(reg_digit(D, kt));  // index of the leading bit
+  int lsb = t - 52;
+  if (lsb < kSubLsb) lsb = kSubLsb;
+  const int wi = (lsb >> 5) - lo, bi = lsb & 31;  // word index relative to lo (may be negative)
+  const unsigned long long w_lo = (unsigned long long)reg_digit(D, wi) | ((unsigned long long)reg_digit(D, wi + 1) << 32);
+  const unsigned long long w_hi = reg_digit(D, wi + 2);
+  unsigned long long mant = bi ? ((w_lo >> bi) | (w_hi << (64 - bi))) : w_lo;
+  const int nbits = t - lsb + 1;  // 1 .. 53
+  mant &= (nbits >= 64) ? ~0ull : ((1ull << nbits) - 1ull);
+  const int rb_i = lsb - 1;
+  const int rw = (rb_i >> 5) - lo;  // word of the round bit, relative to lo
+  const uint32_t rword = reg_digit(D, rw);
+  const uint32_t rbit = (rword >> (rb_i & 31)) & 1u;
+  bool sticky = (rword & ((1u << (rb_i & 31)) - 1u)) != 0u;
+#pragma unroll
+  for (int k = 0; k < kRegDigits; k++) sticky |= (k < rw) && D[k] != 0u;
+  if (rbit && (sticky || (mant & 1ull))) mant += 1ull;
+  if (mant == (1ull << 53)) {
+    mant >>= 1;
+    lsb += 1;
+  }
+  unsigned long long bits;
+  if (mant >= (1ull << 52)) {
+    const int biased = lsb + kE0 + 1075;
+    if (biased >= 2047) bits = 0x7FF0000000000000ull;
+    else bits = ((unsigned long long)biased << 52) | (mant - (1ull << 52));
+  } else {
+    bits = mant;
+  }
+  if (negative) bits |= 0x8000000000000000ull;
+  return __longlong_as_double((long long)bits);
+}
+
+// Either form, by the width of the live range.
+__device__ __forceinline__ double round_digits_fast(const long long* dig, uint32_t* D, int lo, int hi) {
+  const int top = hi + 1 < kNDig ? hi + 1 : kNDig - 1;
+  if (lo <= hi && top - lo + 1 <= kRegDigits) return round_digits_reg(dig, lo, hi);
+  return round_digits_range(dig, D, lo, hi);
+}
+
 // round_digits_range over the non-zero digits of dig (found by a scan).
 static __device__ __noinline__ double round_digits(const long long* dig, uint32_t* D) {
   int lo = kNDig, hi = -1;
@@ -344,7 +425,7 @@ __device__ __forceinline__ double take_and_round(unsigned long long* g, long lon
     }
   }
   __syncthreads();
-  return threadIdx.x == 0 ? round_digits_range(dig, D, range[0], range[1]) : 0.0;
+  return threadIdx.x == 0 ? round_digits_fast(dig, D, range[0], range[1]) : 0.0;
 }
 
 // ------------------------------------------------------------------ EFTs and FPEs
