@@ -399,15 +399,46 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
   __syncthreads();
   Reducer<V, 2> R;
   red_init(R);
-  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
-    const double di = __ldcs(d + i), wi = __ldcs(w + i), ivi = __ldcs(inv + i);
-    const double xi = __fma_rn(rho, di, __ldcs(x + i));
-    const double ri = __fma_rn(nrho, wi, __ldcs(r + i));
+  auto elem = [&](double di, double wi, double ivi, double xi0, double ri0, double& xi, double& ri) {
+    xi = __fma_rn(rho, di, xi0);
+    ri = __fma_rn(nrho, wi, ri0);
     const double zi = __dmul_rn(ivi, ri);
-    __stcs(x + i, xi);
-    __stcs(r + i, ri);
     red_add(R, sacc, 0, zi, ri, p);
     red_add(R, sacc, 1, ri, ri, p);
+  };
+  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {
+    // pairs of elements as double2 (d, w, inv, r are the handle's 256-byte
+    // aligned vectors; x is the caller's, checked here): twice the bytes in
+    // flight per thread
+    const double2* __restrict__ d2 = reinterpret_cast<const double2*>(d);
+    const double2* __restrict__ w2 = reinterpret_cast<const double2*>(w);
+    const double2* __restrict__ v2 = reinterpret_cast<const double2*>(inv);
+    double2* __restrict__ x2 = reinterpret_cast<double2*>(x);
+    double2* __restrict__ r2 = reinterpret_cast<double2*>(r);
+    const int n2 = n >> 1;
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n2; i += gridDim.x * BLOCK) {
+      const double2 dv = __ldcs(d2 + i), wv = __ldcs(w2 + i), vv = __ldcs(v2 + i), xv = __ldcs(x2 + i),
+                    rv = __ldcs(r2 + i);
+      double2 xo, ro;
+      elem(dv.x, wv.x, vv.x, xv.x, rv.x, xo.x, ro.x);
+      elem(dv.y, wv.y, vv.y, xv.y, rv.y, xo.y, ro.y);
+      __stcs(x2 + i, xo);
+      __stcs(r2 + i, ro);
+    }
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+      const int i = n - 1;
+      double xi, ri;
+      elem(d[i], w[i], inv[i], x[i], r[i], xi, ri);
+      x[i] = xi;
+      r[i] = ri;
+    }
+  } else {
+    for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+      double xi, ri;
+      elem(__ldcs(d + i), __ldcs(w + i), __ldcs(inv + i), __ldcs(x + i), __ldcs(r + i), xi, ri);
+      __stcs(x + i, xi);
+      __stcs(r + i, ri);
+    }
   }
   if (red_finish<V, 2, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     if (V == RPCG_FPE && (fs->lost[0] || fs->lost[1])) {
@@ -428,9 +459,21 @@ __global__ void __launch_bounds__(BLOCK) k_pass_c(int n, double* __restrict__ d,
                                                   const double* __restrict__ r, const SolveState* st) {
   if (st->status != 0) return;
   const double g = st->gamma;
-  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
-    const double zi = __dmul_rn(__ldcs(inv + i), __ldcs(r + i));
-    d[i] = __fma_rn(g, d[i], zi);
+  // pairs as double2 (the handle's vectors are 256-byte aligned)
+  const double2* __restrict__ v2 = reinterpret_cast<const double2*>(inv);
+  const double2* __restrict__ r2 = reinterpret_cast<const double2*>(r);
+  double2* __restrict__ d2 = reinterpret_cast<double2*>(d);
+  const int n2 = n >> 1;
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n2; i += gridDim.x * BLOCK) {
+    const double2 vv = __ldcs(v2 + i), rv = __ldcs(r2 + i), dv = d2[i];
+    double2 o;
+    o.x = __fma_rn(g, dv.x, __dmul_rn(vv.x, rv.x));
+    o.y = __fma_rn(g, dv.y, __dmul_rn(vv.y, rv.y));
+    d2[i] = o;
+  }
+  if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) {
+    const int i = n - 1;
+    d[i] = __fma_rn(g, d[i], __dmul_rn(inv[i], r[i]));
   }
 }
 
