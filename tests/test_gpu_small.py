@@ -150,3 +150,20 @@ def test_cluster_plain_converges_and_is_deterministic(rpcg, cuda, oracle_lib):
     assert abs(r1["iterations"] - ref["iterations"]) <= max(2, ref["iterations"] // 20)
     assert r1["iterations"] == r2["iterations"] and np.array_equal(bits(x1), bits(x2))
     assert np.array_equal(bits(h1), bits(h2))
+
+
+@pytest.mark.parametrize("n", [16384, 16385, 16383, 1025])
+def test_cluster_size_boundary(rpcg, cuda, oracle_lib, n):
+    """Band systems (7 entries per row) at the cluster path's limit: 16384 rows
+    fill 16 CTAs of 1024 rows exactly; 16385 rows take the graph path; 16383 and
+    1025 leave a ragged last CTA.  Both paths agree with the oracle."""
+    A = synth.band(n, 3)
+    b = synth.rhs_uniform(n, SEED + n)
+    M = rpcg.Matrix.from_csr(A)
+    assert M.solve_path("exblas") == ("graph" if n > 16384 else "cluster")
+    rc, xc, hc = _solve(M, b, cuda, "exblas", tol=1e-12, max_iter=200)
+    rg, xg, hg = _solve(M, b, cuda, "exblas", block=256, tol=1e-12, max_iter=200)
+    ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, tol=1e-12, max_iter=200, nthreads=4)
+    assert rc["iterations"] == rg["iterations"] == ref["iterations"]
+    assert np.array_equal(bits(xc), bits(ref["x"])) and np.array_equal(bits(xg), bits(ref["x"]))
+    assert np.array_equal(bits(hc), bits(ref["history"]))
