@@ -235,6 +235,23 @@ rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double *b, double *x, int
                                 rpcg_result *res, float *pass_ms, int32_t *launches, void *stream);
 
 /*
+ * rpcg_solve_async -- rpcg_solve without synchronising the stream: the solve
+ * and the writing of *res are enqueued on `stream` and the call returns.
+ *   res   device memory or pinned (page-locked) host memory; valid once the
+ *         stream reaches that point (e.g. after cudaStreamSynchronize).
+ * Same steps, paths and result bits as rpcg_solve, including x = 0 for
+ * b = 0 and the NOT_CONVERGED / FPE_INEXACT statuses (decided on the device).
+ * The arguments are passed to the device by value at the call, so solves may
+ * be enqueued back to back; a handle serves one solve at a time in stream
+ * order (its vectors and state are shared), different handles may run on
+ * different streams concurrently.  Returns RPCG_OK when enqueued; argument
+ * errors (RPCG_ERR_INVALID) and launch failures are returned at once and
+ * nothing is enqueued for them.
+ */
+rpcg_status rpcg_solve_async(rpcg_matrix_t A, const double *b, double *x, int32_t v, const rpcg_opts *o,
+                             rpcg_result *res, void *stream);
+
+/*
  * rpcg_solve_path -- which path rpcg_solve takes for (A, v, o): *path = 1
  * for the cluster-resident launch, 0 for the graph of grid-wide passes.
  * (If the cluster cannot be made resident on this GPU, the first solve

@@ -27,7 +27,7 @@ VARIANTS = {"plain": PLAIN, "exblas": EXBLAS, "fpe": FPE}
 EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
-    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_solve_path", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
+    "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_solve_path", "rpcg_solve_async", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
     "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_solve_profiled", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
     "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_eft_twosum",
     "rpcg_eft_twoprod",
@@ -47,6 +47,15 @@ class Result(ctypes.Structure):
     def as_dict(self):
         return dict(iterations=self.iterations, status=self.status, relres=self.relres, tau=self.tau,
                     fpe_inexact_count=self.fpe_inexact_count, fpe_size_used=self.fpe_size_used)
+
+
+RESULT_BYTES = ctypes.sizeof(Result)
+
+
+def result_from(buf) -> dict:
+    """The rpcg_result in a tensor written by rpcg_solve_async (device or pinned host)."""
+    raw = buf.cpu().numpy().tobytes()[:RESULT_BYTES]
+    return Result.from_buffer_copy(raw).as_dict()
 
 
 class ServerTiming(ctypes.Structure):
@@ -243,6 +252,17 @@ class Matrix:
         if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
             _check(st, "rpcg_solve")
         return r.as_dict()
+
+    def solve_async(self, b, x, res, variant="exblas", stream=None, **opts):
+        """rpcg_solve_async: enqueue the solve on the stream and return at once.
+        res: a uint8 tensor of at least RESULT_BYTES bytes, on the device or
+        in pinned host memory; read it with result_from() after the stream
+        has reached that point."""
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o = make_opts(**opts)
+        assert res.numel() * res.element_size() >= RESULT_BYTES and res.is_contiguous()
+        _check(lib().rpcg_solve_async(self._h, _dptr(b), _dptr(x), v, ctypes.byref(o), ctypes.c_void_p(res.data_ptr()),
+                                      _stream(stream)), "rpcg_solve_async")
 
     def solve_path(self, variant="exblas", **opts) -> str:
         """Which path rpcg_solve takes: "cluster" (one cluster-resident launch)

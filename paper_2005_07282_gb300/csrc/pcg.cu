@@ -858,6 +858,38 @@ static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaSt
 }
 
 // Point the set-up SpMV node at x0 for this call.
+// Asynchronous solves: the arguments reach the device as kernel parameters
+// (captured at launch), so two solves enqueued back to back cannot race on
+// a host staging buffer; the result struct is written by a kernel at the end.
+__global__ void k_set_args(SolveArgs* dst, SolveArgs a) { *dst = a; }
+__global__ void k_set_state(SolveState* dst, SolveState a) { *dst = a; }
+
+// The host-side result logic of rpcg_solve, on the device: status
+// NOT_CONVERGED when the loop stopped at max_iter, FPE_INEXACT for strict fpe
+// solves that saw an inexact dot, x = 0 when b = 0.  Every thread zeroes
+// its part of x in that case; thread 0 of block 0 writes *out.
+__global__ void k_finish_result(const SolveState* st, double tol, int variant, int fpe_strict, double* x, int n,
+                                rpcg_result* out) {
+  const SolveState s = *st;
+  if (s.bzero)
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) x[i] = 0.0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int status = s.status;
+    if (status == RPCG_OK) {
+      if (!(s.rel < tol)) status = RPCG_NOT_CONVERGED;
+      else if (variant == RPCG_FPE && fpe_strict && s.fpe_inexact > 0) status = RPCG_FPE_INEXACT;
+    }
+    rpcg_result r;
+    r.iterations = s.iter;
+    r.status = status;
+    r.relres = s.rel;
+    r.tau = s.tau;
+    r.fpe_inexact_count = s.fpe_inexact;
+    r.fpe_size_used = variant == RPCG_FPE ? s.fpe_p : 0;
+    *out = r;
+  }
+}
+
 static cudaError_t set_x0(rpcg_matrix_t A, cudaGraphNode_t nd, cudaGraphExec_t e, const double* x) {
   cudaKernelNodeParams p{};
   cudaError_t err = cudaGraphKernelNodeGetParams(nd, &p);
@@ -1118,8 +1150,11 @@ rpcg_status rpcg_spmv(rpcg_matrix_t A, const double* x, double* y, void* stream)
   return RPCG_OK;
 }
 
+// async: enqueue only; *res is written on the device (device or pinned host
+// memory) by k_finish_result and the stream is not synchronised.
 static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32_t v, const rpcg_opts* o,
-                              rpcg_result* res, cudaStream_t s, float* pass_ms = nullptr, int* launches = nullptr) {
+                              rpcg_result* res, cudaStream_t s, float* pass_ms = nullptr, int* launches = nullptr,
+                              bool async = false) {
   rpcg_opts opt;
   if (o) opt = *o;
   else rpcg_opts_default(&opt);
@@ -1132,6 +1167,16 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == block, "block must be 0, 128, 256 or 512");
   if (v == RPCG_FPE && opt.grid > 512) opt.grid = 512;
   const int n = A->m.n;
+  if (n == 0 && async) {
+    // nothing to solve: the result of an empty system, written in stream order
+    SolveState zero{};
+    zero.status = RPCG_OK;
+    k_set_state<<<1, 1, 0, s>>>(A->state, zero);
+    if (opt.history) RPCG_CUDA_TRY(cudaMemsetAsync(opt.history, 0, sizeof(double), s));
+    k_finish_result<<<1, 32, 0, s>>>(A->state, INFINITY, v, 0, x, 0, res);
+    RPCG_CUDA_TRY(cudaGetLastError());
+    return RPCG_OK;
+  }
   if (n == 0) {
     res->iterations = 0;
     res->status = RPCG_OK;
@@ -1157,16 +1202,23 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
   }
   SolveArgs* ha = A->h_args;
   if (!small) {
-  ha->b = b;
-  ha->x = x;
-  ha->history = opt.history;
-  ha->tol = opt.tol;
-  ha->max_iter = opt.max_iter;
-  ha->fpe_size = opt.fpe_size;
-  ha->fpe_strict = opt.fpe_strict;
-  ha->variant = v;
-  ha->use_cond = eager ? 0 : 1;
-  RPCG_CUDA_TRY(cudaMemcpyAsync(A->args, ha, sizeof(SolveArgs), cudaMemcpyHostToDevice, s));
+  SolveArgs av{};
+  av.b = b;
+  av.x = x;
+  av.history = opt.history;
+  av.tol = opt.tol;
+  av.max_iter = opt.max_iter;
+  av.fpe_size = opt.fpe_size;
+  av.fpe_strict = opt.fpe_strict;
+  av.variant = v;
+  av.use_cond = eager ? 0 : 1;
+  if (async) {
+    k_set_args<<<1, 1, 0, s>>>(A->args, av);
+    RPCG_CUDA_TRY(cudaGetLastError());
+  } else {
+    *ha = av;
+    RPCG_CUDA_TRY(cudaMemcpyAsync(A->args, ha, sizeof(SolveArgs), cudaMemcpyHostToDevice, s));
+  }
   if (eager) {
     rpcg_status st;
 #define RPCG_EAGER(VV, BB) st = run_eager<VV, BB>(A, opt.grid, x, s, pass_ms, launches)
@@ -1182,6 +1234,12 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
   } else {
     RPCG_CUDA_TRY(cudaGraphLaunch(exec, s));
   }
+  }
+  if (async) {
+    const int g = std::max(1, std::min((n + 255) / 256, sm_count() * 4));
+    k_finish_result<<<g, 256, 0, s>>>(A->state, opt.tol, v, opt.fpe_strict, x, n, res);
+    RPCG_CUDA_TRY(cudaGetLastError());
+    return RPCG_OK;
   }
   RPCG_CUDA_TRY(cudaMemcpyAsync(A->h_state, A->state, sizeof(SolveState), cudaMemcpyDeviceToHost, s));
   RPCG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -1224,6 +1282,15 @@ rpcg_status rpcg_solve_profiled(rpcg_matrix_t A, const double* b, double* x, int
     if (launches) launches[i] = 0;
   }
   return solve_impl(A, b, x, v, o, res, (cudaStream_t)stream, pass_ms, launches);
+}
+
+rpcg_status rpcg_solve_async(rpcg_matrix_t A, const double* b, double* x, int32_t v, const rpcg_opts* o,
+                             rpcg_result* res, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(A != nullptr, "A is NULL");
+  RPCG_CHECK_ARG(res != nullptr, "res is NULL");
+  RPCG_CHECK_ARG(A->m.n == 0 || (b && x), "b or x is NULL");
+  return solve_impl(A, b, x, v, o, res, (cudaStream_t)stream, nullptr, nullptr, true);
 }
 
 rpcg_status rpcg_solve_path(rpcg_matrix_t A, int32_t v, const rpcg_opts* o, int32_t* path) {
