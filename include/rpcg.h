@@ -301,6 +301,20 @@ rpcg_status rpcg_batch_destroy(rpcg_batch_t B);
 rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double *const *b, double *const *x, int32_t v, const rpcg_opts *o,
                              rpcg_result *res, void *stream);
 /*
+ * rpcg_batch_solve_async -- rpcg_batch_solve without synchronising the
+ * stream: the batch run and the writing of res[0..count-1] (device memory or
+ * pinned host memory) are enqueued on `stream` and the call returns.  Same
+ * results as rpcg_batch_solve (NOT_CONVERGED and x = 0 for b = 0 decided on
+ * the device).  It does not autotune: a zero o->block / o->tile takes the
+ * autotuned shape if an earlier rpcg_batch_solve chose one, else 128 and
+ * 1024 rows.  A batch runs one solve at a time in stream order (its handles'
+ * vectors are shared); the call waits only if its previous upload of the
+ * system table has not yet executed.  Argument errors return at once.
+ */
+rpcg_status rpcg_batch_solve_async(rpcg_batch_t B, const double *const *b, double *const *x, int32_t v,
+                                   const rpcg_opts *o, rpcg_result *res, void *stream);
+
+/*
  * rpcg_batch_solve_profiled -- rpcg_batch_solve with the batch kernels
  * launched one by one from the host and CUDA events recorded on `stream`
  * around each kind of pass; bit-identical results.  A zero o->block or

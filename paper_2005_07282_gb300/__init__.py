@@ -28,7 +28,7 @@ EXPORTS = [
     "rpcg_opts_default", "rpcg_status_string", "rpcg_last_error", "rpcg_create", "rpcg_destroy",
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
     "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_solve_path", "rpcg_solve_async", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
-    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_solve_profiled", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
+    "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_solve_profiled", "rpcg_batch_solve_async", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
     "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_eft_twosum",
     "rpcg_eft_twoprod",
 ]
@@ -56,6 +56,12 @@ def result_from(buf) -> dict:
     """The rpcg_result in a tensor written by rpcg_solve_async (device or pinned host)."""
     raw = buf.cpu().numpy().tobytes()[:RESULT_BYTES]
     return Result.from_buffer_copy(raw).as_dict()
+
+
+def results_from(buf, count) -> list:
+    """The count rpcg_result records in a tensor written by rpcg_batch_solve_async."""
+    raw = buf.cpu().numpy().tobytes()
+    return [Result.from_buffer_copy(raw[k * RESULT_BYTES:(k + 1) * RESULT_BYTES]).as_dict() for k in range(count)]
 
 
 class ServerTiming(ctypes.Structure):
@@ -335,6 +341,20 @@ class Batch:
         if st in (ERR_INVALID, ERR_OOM, ERR_CUDA):
             _check(st, "rpcg_batch_solve")
         return [r.as_dict() for r in res]
+
+    def solve_async(self, bs, xs, res, variant="exblas", stream=None, **opts):
+        """rpcg_batch_solve_async: enqueue and return; res: a uint8 tensor of at
+        least len(mats) * RESULT_BYTES bytes (device or pinned host), read with
+        results_from() once the stream has reached that point."""
+        n = len(self.mats)
+        assert len(bs) == n and len(xs) == n
+        assert res.numel() * res.element_size() >= n * RESULT_BYTES and res.is_contiguous()
+        barr = (ctypes.c_void_p * n)(*[_dptr(t).value for t in bs])
+        xarr = (ctypes.c_void_p * n)(*[_dptr(t).value for t in xs])
+        v = VARIANTS[variant] if isinstance(variant, str) else int(variant)
+        o = make_opts(**opts)
+        _check(lib().rpcg_batch_solve_async(self._h, barr, xarr, v, ctypes.byref(o), ctypes.c_void_p(res.data_ptr()),
+                                            _stream(stream)), "rpcg_batch_solve_async")
 
     def solve_profiled(self, bs, xs, variant="exblas", stream=None, **opts):
         """solve() launched pass by pass with events; returns (results,

@@ -51,6 +51,7 @@ struct rpcg_batch_s {
   std::map<std::tuple<int, int, int>, cudaGraphExec_t> graphs;  // (variant, block, tile)
   std::map<std::tuple<int, int, int>, cudaGraph_t> graph_defs;
   int tuned_block = 0, tuned_tile = 0;
+  cudaEvent_t uploaded = nullptr;  // the last upload of h_sys (rewritten only after it ran)
 };
 
 namespace rpcg {
@@ -210,6 +211,7 @@ static void batch_free(rpcg_batch_t B) {
     cudaFree(kv.second.partials);
   }
   cudaFree(B->d_aprefix);
+  if (B->uploaded) cudaEventDestroy(B->uploaded);
   cudaFree(B->d_sys);
   cudaFree(B->d_state);
   cudaFree(B->d_red);
@@ -233,10 +235,40 @@ static rpcg_status batch_run(rpcg_batch_t B, const double* const* b, double* con
   cudaGraphExec_t e = nullptr;
   rpcg_status st = batch_get_graph(B, v, block, tile, &e);
   if (st != RPCG_OK) return st;
+  // the pinned table is read by the copy when it runs: wait for the previous
+  // copy (usually long done) before rewriting it
+  if (B->uploaded) RPCG_CUDA_TRY(cudaEventSynchronize(B->uploaded));
   batch_upload(B, b, x, o);
   RPCG_CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys, B->count * sizeof(SysDev), cudaMemcpyHostToDevice, s));
+  if (!B->uploaded) RPCG_CUDA_TRY(cudaEventCreateWithFlags(&B->uploaded, cudaEventDisableTiming));
+  RPCG_CUDA_TRY(cudaEventRecord(B->uploaded, s));
   RPCG_CUDA_TRY(cudaGraphLaunch(e, s));
   return RPCG_OK;
+}
+
+// The per-system results of a batch run, on the device (the host logic of
+// batch_results): NOT_CONVERGED when a system stopped at max_iter, x = 0
+// for b = 0, an empty system OK with nothing done.  One block per system.
+static __global__ void k_b_results(const SysDev* __restrict__ sys, const SysState* __restrict__ st, int count,
+                                   rpcg_result* out) {
+  for (int s = blockIdx.x; s < count; s += gridDim.x) {
+    const SysState t = st[s];
+    const int n = sys[s].m.n;
+    if (n > 0 && t.bzero)
+      for (int i = threadIdx.x; i < n; i += blockDim.x) sys[s].x[i] = 0.0;
+    if (threadIdx.x == 0) {
+      rpcg_result r{0, RPCG_OK, 0.0, 0.0, 0, 0};
+      if (n > 0) {
+        int status = t.status;
+        if (status == RPCG_OK && !(t.rel < sys[s].tol)) status = RPCG_NOT_CONVERGED;
+        r.iterations = t.iter;
+        r.status = status;
+        r.relres = t.rel;
+        r.tau = t.tau;
+      }
+      out[s] = r;
+    }
+  }
 }
 
 // The batch loop launched kernel by kernel from the host, with events
@@ -458,6 +490,29 @@ rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double* const* b, do
                          : batch_eager<RPCG_EXBLAS, 256>(B, tile, s, pass_ms, launches);
   if (st != RPCG_OK) return st;
   return batch_results(B, x, opt, res, s);
+}
+
+rpcg_status rpcg_batch_solve_async(rpcg_batch_t B, const double* const* b, double* const* x, int32_t v,
+                                   const rpcg_opts* o, rpcg_result* res, void* stream) {
+  clear_error();
+  RPCG_CHECK_ARG(B != nullptr && b != nullptr && x != nullptr && res != nullptr, "NULL argument");
+  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS, "batched solves support the plain and exblas variants");
+  rpcg_opts opt;
+  if (o) opt = *o;
+  else rpcg_opts_default(&opt);
+  RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
+  RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
+  RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
+  for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
+  cudaStream_t s = (cudaStream_t)stream;
+  // no autotuning here (it times runs): the tuned shape if there is one, else 128 x 1024
+  const int block = opt.block ? opt.block : (B->tuned_block ? B->tuned_block : 128);
+  const int tile = opt.tile ? opt.tile : (B->tuned_tile ? B->tuned_tile : 1024);
+  rpcg_status st = batch_run(B, b, x, v, opt, block, tile, s);
+  if (st != RPCG_OK) return st;
+  k_b_results<<<std::max(1, std::min(B->count, sm_count() * 8)), 256, 0, s>>>(B->d_sys, B->d_state, B->count, res);
+  RPCG_CUDA_TRY(cudaGetLastError());
+  return RPCG_OK;
 }
 
 rpcg_status rpcg_batch_tuned(rpcg_batch_t B, int32_t* block, int32_t* tile) {

@@ -159,3 +159,33 @@ def test_batch_more_systems_than_shared_prefix(rpcg, cuda, oracle_lib):
         ref = oracle_lib.pcg(mats[i], rhs[i], variant=oracle_lib.EXACT, tol=1e-12, max_iter=100)
         assert res[i]["iterations"] == ref["iterations"] and res[i]["status"] == ref["status"], i
         assert np.array_equal(bits(xs[i].cpu().numpy()), bits(ref["x"])), i
+
+
+def test_batch_async_equals_sync(rpcg, cuda, oracle_lib):
+    """rpcg_batch_solve_async: enqueued without synchronising; the per-system
+    results (device or pinned host memory) and iterates equal the synchronous
+    batch solve, including a b = 0 system and an empty one."""
+    import torch
+    mats, rhs = _systems()
+    E = synth.CSR(0, np.zeros(1, dtype=np.int32), np.zeros(0, dtype=np.int32), np.zeros(0))
+    mats = mats + [E, mats[0].__class__(mats[0].n, mats[0].rowptr.copy(), mats[0].col.copy(), mats[0].val.copy())]
+    rhs = rhs + [np.zeros(0), np.zeros(mats[0].n)]
+    Ms = [rpcg.Matrix.from_csr(A) for A in mats]
+    bs = [_dev(b, cuda) for b in rhs]
+    B = rpcg.Batch(Ms)
+    xs_sync = [torch.ones(A.n, dtype=torch.float64, device=cuda) for A in mats]
+    rs = B.solve(bs, xs_sync, variant="exblas", tol=1e-10, max_iter=3000, tile=64, block=128)
+    for pinned in (False, True):
+        xs = [torch.ones(A.n, dtype=torch.float64, device=cuda) for A in mats]
+        nbytes = len(mats) * rpcg.RESULT_BYTES
+        res = torch.zeros(nbytes, dtype=torch.uint8).pin_memory() if pinned else \
+            torch.zeros(nbytes, dtype=torch.uint8, device=cuda)
+        B.solve_async(bs, xs, res, variant="exblas", tol=1e-10, max_iter=3000, tile=64, block=128)
+        torch.cuda.synchronize()
+        ra = rpcg.results_from(res, len(mats))
+        for i in range(len(mats)):
+            assert ra[i]["status"] == rs[i]["status"] and ra[i]["iterations"] == rs[i]["iterations"], i
+            assert bits([ra[i]["relres"]])[0] == bits([rs[i]["relres"]])[0], i
+            assert torch.equal(xs[i].view(torch.int64), xs_sync[i].view(torch.int64)), i
+    assert ra[-1]["iterations"] == 0 and not xs[-1].any().item()   # b = 0: x = 0
+    assert ra[-2] == {**ra[-2], "status": 0, "iterations": 0}     # the empty system
