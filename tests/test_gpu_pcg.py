@@ -260,3 +260,35 @@ def test_pcg_fpe_adaptive_size(rpcg, cuda, oracle_lib):
     x1 = torch.zeros(A.n, dtype=torch.float64, device=cuda)
     r1 = M.solve(b, x1, variant="fpe", tol=1e-10, max_iter=2000, fpe_size=1)
     assert r1["fpe_size_used"] == 1 and r1["fpe_inexact_count"] > 0
+
+
+def test_spmv_single_step_all_magnitudes(rpcg, cuda, oracle_lib):
+    """A diagonal matrix makes every row a single step fma(a_ii, x_i, +0):
+    normal, zero, subnormal, overflowing, infinite and NaN operands and
+    results (and rounding ties) all equal the oracle's fma bit for bit (NaNs
+    as NaNs)."""
+    n = 1 << 20
+    rng = np.random.default_rng(11)
+    def draw(k):
+        m = rng.uniform(1.0, 2.0, k) * rng.choice([-1.0, 1.0], k)
+        e = rng.integers(-1074, 1024, k)
+        v = np.ldexp(m, e)
+        special = rng.random(k)
+        v[special < 0.01] = 0.0
+        v[(special >= 0.01) & (special < 0.015)] = -0.0
+        v[(special >= 0.015) & (special < 0.02)] = np.inf
+        v[(special >= 0.02) & (special < 0.022)] = np.nan
+        v[(special >= 0.022) & (special < 0.05)] = np.ldexp(rng.uniform(0, 1, k), -1022)[(special >= 0.022) & (special < 0.05)]
+        return v
+    d, x = draw(n), draw(n)
+    # products near the edges of the normal range and exact ties
+    d[:1000] = np.ldexp(1.0 + np.arange(1000) * 2.0 ** -52, -511)
+    x[:1000] = np.ldexp(1.0 + 2.0 ** -52, -511)
+    d[1000:2000] = np.ldexp(1.5, 511)
+    x[1000:2000] = np.ldexp(1.0 + np.arange(1000) * 2.0 ** -40, 512)
+    A = synth.CSR(n, np.arange(n + 1, dtype=np.int32), np.arange(n, dtype=np.int32), d)
+    want = oracle_lib.spmv(A, x)
+    got = rpcg.Matrix.from_csr(A).spmv(_dev(x, cuda)).cpu().numpy()
+    nan = np.isnan(want)
+    assert np.array_equal(np.isnan(got), nan)
+    assert np.array_equal(bits(got[~nan]), bits(want[~nan]))
