@@ -63,24 +63,28 @@ def test_async_equals_sync(rpcg, cuda, oracle_lib, kind, variant, kw, path):
     _same(rpcg.result_from(res), x.cpu().numpy(), rs, xs)
 
 
-def test_async_back_to_back_on_one_handle(rpcg, cuda, oracle_lib):
-    """Two solves enqueued on one handle before either runs: each sees its own
-    arguments (passed by value at the call)."""
+@pytest.mark.parametrize("kind,kw", [("p7_12", {}), ("p27_14", {}), ("p7_12", {"block": 256}),
+                                     ("p27_30", {})])
+def test_async_back_to_back_on_one_handle(rpcg, cuda, oracle_lib, kind, kw):
+    """Two solves enqueued on one handle before either runs, on the cluster
+    path and on the graph path (whose x0 node is updated between the two
+    launches): each sees its own arguments (passed by value at the call)."""
     import torch
-    for A in (synth.poisson7(12), synth.poisson27(14)):
-        M = rpcg.Matrix.from_csr(A)
-        b1 = _dev(synth.rhs_uniform(A.n, SEED + 1), cuda)
-        b2 = _dev(synth.rhs_uniform(A.n, SEED + 2), cuda)
-        r1s, x1s = _sync(M, b1, cuda, tol=1e-9, max_iter=500)
-        r2s, x2s = _sync(M, b2, cuda, tol=1e-6, max_iter=500)
-        x1 = torch.zeros(A.n, dtype=torch.float64, device=cuda)
-        x2 = torch.zeros(A.n, dtype=torch.float64, device=cuda)
-        res1, res2 = _res_buf(rpcg, cuda), _res_buf(rpcg, cuda, pinned=True)
-        M.solve_async(b1, x1, res1, tol=1e-9, max_iter=500)
-        M.solve_async(b2, x2, res2, tol=1e-6, max_iter=500)
-        torch.cuda.synchronize()
-        _same(rpcg.result_from(res1), x1.cpu().numpy(), r1s, x1s)
-        _same(rpcg.result_from(res2), x2.cpu().numpy(), r2s, x2s)
+    A = {"p7_12": lambda: synth.poisson7(12), "p27_14": lambda: synth.poisson27(14),
+         "p27_30": lambda: synth.poisson27(30)}[kind]()
+    M = rpcg.Matrix.from_csr(A)
+    b1 = _dev(synth.rhs_uniform(A.n, SEED + 1), cuda)
+    b2 = _dev(synth.rhs_uniform(A.n, SEED + 2), cuda)
+    r1s, x1s = _sync(M, b1, cuda, tol=1e-9, max_iter=500, **kw)
+    r2s, x2s = _sync(M, b2, cuda, x0=np.full(A.n, 0.5), tol=1e-6, max_iter=500, **kw)
+    x1 = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    x2 = _dev(np.full(A.n, 0.5), cuda)
+    res1, res2 = _res_buf(rpcg, cuda), _res_buf(rpcg, cuda, pinned=True)
+    M.solve_async(b1, x1, res1, tol=1e-9, max_iter=500, **kw)
+    M.solve_async(b2, x2, res2, tol=1e-6, max_iter=500, **kw)
+    torch.cuda.synchronize()
+    _same(rpcg.result_from(res1), x1.cpu().numpy(), r1s, x1s)
+    _same(rpcg.result_from(res2), x2.cpu().numpy(), r2s, x2s)
 
 
 def test_async_two_handles_two_streams(rpcg, cuda, oracle_lib):
