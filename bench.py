@@ -209,11 +209,12 @@ class ClockSampler:
 
 # ---------------------------------------------------------------- CPU oracle leg
 
-def cpu_oracle_rate(A, b, iters, tol):
-    """The oracle as it stands, on all host cores: iterations per second of
-    its PCG loop (set-up excluded) over a bounded number of iterations."""
+def cpu_oracle_rate(A, b, iters, tol, nthreads=None):
+    """The oracle as it stands, on all host cores (or nthreads): iterations
+    per second of its PCG loop (set-up excluded) over a bounded number of
+    iterations."""
     import oracle
-    nt = oracle.default_threads()
+    nt = oracle.default_threads() if nthreads is None else nthreads
     r = oracle.pcg(A, b, variant=oracle.EXACT, tol=tol, max_iter=iters, nthreads=nt)
     return r["iterations"] / max(r["loop_seconds"], 1e-9), r["iterations"], r["loop_seconds"], nt
 
@@ -435,8 +436,10 @@ def gpu_arm(args, rank, world, local_rank):
             import oracle
             b_host = d_b.cpu().numpy()
             crate, cit, csec, cores = cpu_oracle_rate(A, b_host, 3, args.tol)
+            srate, sit, ssec, _ = cpu_oracle_rate(A, b_host, 1, args.tol, nthreads=1)
             cpu = {"value": crate, "unit": "iters/s", "cores": cores, "kind": "oracle",
-                   "sample": f"{cit} exact-dot PCG iterations of the same system ({csec:.1f} s, set-up excluded)"}
+                   "sample": f"{cit} exact-dot PCG iterations of the same system ({csec:.1f} s, set-up excluded)",
+                   "single_thread": {"value": srate, "sample": f"{sit} iteration on one core ({ssec:.1f} s)"}}
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
