@@ -292,3 +292,42 @@ def test_spmv_single_step_all_magnitudes(rpcg, cuda, oracle_lib):
     nan = np.isnan(want)
     assert np.array_equal(np.isnan(got), nan)
     assert np.array_equal(bits(got[~nan]), bits(want[~nan]))
+
+
+@pytest.mark.parametrize("kw", [{}, {"block": 256}])
+def test_pcg_storage_order_duplicates_and_stored_zeros(rpcg, cuda, oracle_lib, kw):
+    """CSR as stored, not as a canonical matrix: columns unsorted within rows,
+    explicitly stored zeros, and a diagonal entry stored twice (the last one
+    in storage order is a_ii; the SpMV adds both).  Every row's fma chain
+    follows storage order, so both solver paths match the oracle bit for bit."""
+    import torch
+    A0 = synth.poisson7(10)
+    rng = np.random.default_rng(5)
+    rowptr, cols, vals = [0], [], []
+    for i in range(A0.n):
+        c = list(A0.col[A0.rowptr[i]:A0.rowptr[i + 1]])
+        v = list(A0.val[A0.rowptr[i]:A0.rowptr[i + 1]])
+        perm = rng.permutation(len(c))
+        c = [c[k] for k in perm]
+        v = [v[k] for k in perm]
+        if i % 3 == 0:                 # a stored zero
+            c.append(c[0]); v.append(0.0)
+        if i % 5 == 0:                 # the diagonal twice: 0.5 + 5.5 (the second one is a_ii)
+            k = c.index(i)
+            v[k] = 0.5
+            c.append(i); v.append(5.5)
+        rowptr.append(rowptr[-1] + len(c))
+        cols += c
+        vals += v
+    A = synth.CSR(A0.n, np.array(rowptr, dtype=np.int32), np.array(cols, dtype=np.int32), np.array(vals))
+    b = synth.rhs_uniform(A.n, SEED + 77)
+    M = rpcg.Matrix.from_csr(A)
+    x = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+    hist = torch.full((1001,), float("nan"), dtype=torch.float64, device=cuda)
+    r = M.solve(_dev(b, cuda), x, variant="exblas", tol=1e-10, max_iter=1000, history=hist, **kw)
+    ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, tol=1e-10, max_iter=1000)
+    assert r["status"] == ref["status"] and r["iterations"] == ref["iterations"]
+    assert np.array_equal(bits(x.cpu().numpy()), bits(ref["x"]))
+    assert np.array_equal(bits(hist[: r["iterations"] + 1].cpu().numpy()), bits(ref["history"][: r["iterations"] + 1]))
+    y = M.spmv(_dev(b, cuda)).cpu().numpy()
+    assert np.array_equal(bits(y), bits(oracle_lib.spmv(A, b)))
