@@ -36,7 +36,6 @@ int sm_count() {
 // ------------------------------------------------------------------ scratch
 constexpr int kDotBlock = 256;
 constexpr int kDotMaxGrid = 2048;
-constexpr int kFpeDotMaxGrid = 640;  // CTA expansions (the scratch must fit the 64 KiB no-allocation array); the last CTA pre-merges them kDotBlock-strided
 
 struct DotScratch {
   // zeroed before every launch (header)
@@ -45,7 +44,6 @@ struct DotScratch {
   unsigned int flags;  // bit 0: non-finite input; bit 1: an expansion lost bits
   // written before being read (no clearing needed)
   double partials[kDotMaxGrid];
-  double fpe[kFpeDotMaxGrid * kFpeMax];
 };
 constexpr size_t kDotScratchHeader = offsetof(DotScratch, partials);
 
@@ -120,29 +118,6 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
 }
 
 // ------------------------------------------------------------------ FPE dot
-// Fixed-order tree merge of BLOCK expansions held in shared memory
-// (sf[t * kFpeMax + i]); the result ends in slot 0.  Returns (via *lost)
-// whether any fpesum dropped a term.
-template <int BLOCK>
-__device__ void fpe_tree(double* sf, int count, int p, int* lost) {
-  for (int stride = 1; stride < count; stride <<= 1) {
-    __syncthreads();
-    const int t = threadIdx.x;
-    if ((t % (2 * stride)) == 0 && t + stride < count) {
-      double A[kFpeMax], B[kFpeMax];
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) {
-        A[i] = sf[t * kFpeMax + i];
-        B[i] = sf[(t + stride) * kFpeMax + i];
-      }
-      if (fpe_sum(A, B, p)) atomicOr(lost, 1);
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = A[i];
-    }
-  }
-  __syncthreads();
-}
-
 // Elementwise Alg. 1 (which = 0) or Alg. 2 (which = 1) on the integer pipe;
 // zero, non-finite and out-of-range elements take the FP64 formulas, so
 // every output equals the FP64 algorithm's.
@@ -173,15 +148,20 @@ __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __r
   }
 }
 
+// FPE dot (Sec. 4.2): each thread accumulates its products into a result
+// and an error expansion (Algs. 2 and 4, early exit) and merges the two
+// (Alg. 3); the threads' expansions then meet exactly in the long
+// accumulator and are rounded once, so the merge loses nothing and *exact
+// reports whether any thread's expansion lost bits (or a product fell below
+// twoprod's exact range).
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,
                                                    const double* __restrict__ b, int p, DotScratch* ws, double* out,
                                                    int32_t* exact) {
-  __shared__ double sf[BLOCK * kFpeMax];
-  __shared__ int slost;
+  __shared__ unsigned long long sacc[kNDig * kCopies];
   __shared__ long long sdig[kNDig];
   __shared__ uint32_t sD[kNDig];
-  if (threadIdx.x == 0) slost = 0;
+  smem_acc_zero(sacc);
   double res[kFpeMax], err[kFpeMax];
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) res[i] = err[i] = 0.0;
@@ -220,45 +200,30 @@ __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __re
     }
   }
   lost |= fpe_sum(res, err, p);
-  if (nonfinite) atomicOr(&ws->flags, 4u);
+  Window win;
+  window_init(win);
+  const int copy = threadIdx.x & (kCopies - 1);
 #pragma unroll
-  for (int i = 0; i < kFpeMax; i++) sf[threadIdx.x * kFpeMax + i] = res[i];
-  __syncthreads();
-  if (lost) atomicOr(&slost, 1);
-  fpe_tree<BLOCK>(sf, BLOCK, p, &slost);
-  if (threadIdx.x == 0) {
-    for (int i = 0; i < kFpeMax; i++) ws->fpe[blockIdx.x * kFpeMax + i] = sf[i];
-    if (slost) atomicOr(&ws->flags, 2u);
-  }
-  if (is_last_block(&ws->counter)) {
-    const int g = gridDim.x;
-    if (threadIdx.x == 0) slost = 0;
-    __syncthreads();
-    {
-      // thread t merges CTA expansions t, t + BLOCK, t + 2 BLOCK, ... in
-      // that order, then the fixed tree merges the BLOCK partial results
-      const int t = threadIdx.x;
-      double A[kFpeMax], B[kFpeMax];
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) A[i] = t < g ? __ldcg(&ws->fpe[t * kFpeMax + i]) : 0.0;
-      bool l2 = false;
-      for (int c = t + BLOCK; c < g; c += BLOCK) {
-#pragma unroll
-        for (int i = 0; i < kFpeMax; i++) B[i] = __ldcg(&ws->fpe[c * kFpeMax + i]);
-        l2 |= fpe_sum(A, B, p);
-      }
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = A[i];
-      if (l2) atomicOr(&slost, 1);
+  for (int i = 0; i < kFpeMax; i++) {
+    if (i < p && !is_zero_bits(res[i])) {
+      const ExactProd e = exact_product(res[i], 1.0);
+      nonfinite |= e.bad;
+      exact_deposit(win, sacc, copy, e);
     }
-    fpe_tree<BLOCK>(sf, g < BLOCK ? g : BLOCK, p, &slost);
+  }
+  window_flush(win, sacc, copy);
+  if (nonfinite) atomicOr(&ws->flags, 4u);
+  if (lost) atomicOr(&ws->flags, 2u);
+  __syncthreads();
+  smem_to_global(sacc, ws->digits);
+  if (is_last_block(&ws->counter)) {
+    __shared__ int srange[2];
+    const double v = take_and_round(ws->digits, sdig, sD, srange);
     if (threadIdx.x == 0) {
       const unsigned int f = atomicExch(&ws->flags, 0u);
-      bool fin = !(f & 4u);
-      for (int i = 0; i < p; i++) fin &= isfinite(sf[i]);
-      const bool ok = fin && !(f & 2u) && !slost;
-      *out = fin ? exact_sum_terms(sf, p, sdig, sD) : __longlong_as_double(0x7FF8000000000000ll);
-      *exact = ok ? 1 : 0;
+      const bool fin = !(f & 4u);
+      *out = fin ? v : __longlong_as_double(0x7FF8000000000000ll);
+      *exact = (fin && !(f & 2u)) ? 1 : 0;
       ws->counter = 0;
     }
   }
@@ -361,7 +326,7 @@ static rpcg_status dot_common(int kind, int64_t n, const double* a, const double
     if (kind == 0) {
       launch_dot_exact(n, a, b, ws, out, s);
     } else if (kind == 1) {
-      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kFpeDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
+      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
     } else {
       k_dot_plain<kDotBlock><<<dot_grid(n, 4, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
     }

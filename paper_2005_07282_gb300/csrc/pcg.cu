@@ -38,15 +38,11 @@ struct PassScratch {
   unsigned int counter;                 // CTAs arrived (reset by the last CTA)
   unsigned int flags;                   // bit 0: non-finite operand; bit 1 + j: dot j lost bits (fpe)
   double partials[3][kMaxPassGrid];     // plain: CTA partial sums
-  double fpe[3][512][kFpeMax];          // fpe: CTA expansions (grid <= 512 for fpe)
 };
 
 // ------------------------------------------------------------------ reducers
 
-constexpr int kFpeTree = 512;  // expansions merged by one CTA (threads of a CTA, or CTAs of a grid)
-
 struct FinalScratch {  // shared memory of the CTA and grid reductions
-  double* fpe;         // kFpeTree expansions (fpe variant only)
   long long dig[kNDig];
   uint32_t D[kNDig];
   double sw[32];
@@ -84,19 +80,18 @@ __device__ __forceinline__ void red_init(Reducer<V, NACC>& R) {
   R.bad = false;
 }
 
-// shared memory of the reducers: exact needs NACC accumulators with copies
+// shared memory of the reducers: exact and fpe need NACC long accumulators
+// with copies (fpe: the threads' expansions meet there)
 template <int V, int NACC>
 __host__ __device__ constexpr size_t red_smem_bytes() {
-  return V == RPCG_EXBLAS ? (size_t)NACC * kNDig * kCopies * sizeof(unsigned long long)
-                          : (V == RPCG_FPE ? (size_t)kFpeTree * kFpeMax * sizeof(double) : 0);
+  return V != RPCG_PLAIN ? (size_t)NACC * kNDig * kCopies * sizeof(unsigned long long) : 0;
 }
 
-// Carve the reducer's shared memory: [exact accumulators | fpe tree] then FinalScratch.
+// Carve the reducer's shared memory: [long accumulators] then FinalScratch.
 template <int V, int NACC>
 __device__ __forceinline__ FinalScratch* red_carve(unsigned char* base, unsigned long long*& sacc) {
   sacc = reinterpret_cast<unsigned long long*>(base);
   FinalScratch* fs = reinterpret_cast<FinalScratch*>(base + red_smem_bytes<V, NACC>());
-  if (threadIdx.x == 0) fs->fpe = reinterpret_cast<double*>(base);
   return fs;
 }
 
@@ -115,25 +110,6 @@ __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long*
   }
 }
 
-template <int BLOCK>
-__device__ void fpe_tree_pass(double* sf, int count, int p, int* lost) {
-  for (int stride = 1; stride < count; stride <<= 1) {
-    __syncthreads();
-    for (int t = threadIdx.x * 2 * stride; t + stride < count; t += BLOCK * 2 * stride) {
-      double A[kFpeMax], B[kFpeMax];
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) {
-        A[i] = sf[t * kFpeMax + i];
-        B[i] = sf[(t + stride) * kFpeMax + i];
-      }
-      if (fpe_sum(A, B, p)) atomicOr(lost, 1);
-#pragma unroll
-      for (int i = 0; i < kFpeMax; i++) sf[t * kFpeMax + i] = A[i];
-    }
-  }
-  __syncthreads();
-}
-
 // CTA part of the reduction (all threads), then the grid part by the last
 // CTA.  Returns true in every thread of the last CTA; fs->value[j] then
 // holds the dot values and fs->lost[j] whether an expansion lost bits (fpe)
@@ -149,22 +125,30 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
 #pragma unroll
     for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, ws->digits[j]);
   } else if constexpr (V == RPCG_FPE) {
-    if (R.bad) atomicOr(&ws->flags, 1u);
+    // each thread merges its error expansion into its result expansion
+    // (Alg. 3); the threads' expansions then meet exactly in the long
+    // accumulator, so the merge loses nothing and the flag reports what the
+    // threads' own expansions lost
+    bool bad = R.bad;
 #pragma unroll  // constant indices keep the expansions in registers
     for (int j = 0; j < NACC; j++) {
       R.lost[j] |= fpe_sum(R.res[j], R.err[j], p);
-      __syncthreads();
-      if (threadIdx.x == 0) fs->slost = 0;
+      if (R.lost[j]) atomicOr(&ws->flags, 2u << j);
+      window_init(R.win[j]);
 #pragma unroll
-      for (int i = 0; i < kFpeMax; i++) fs->fpe[threadIdx.x * kFpeMax + i] = R.res[j][i];
-      __syncthreads();
-      if (R.lost[j]) atomicOr(&fs->slost, 1);
-      fpe_tree_pass<BLOCK>(fs->fpe, BLOCK, p, &fs->slost);
-      if (threadIdx.x == 0) {
-        for (int i = 0; i < kFpeMax; i++) ws->fpe[j][blockIdx.x][i] = fs->fpe[i];
-        if (fs->slost) atomicOr(&ws->flags, 2u << j);
+      for (int i = 0; i < kFpeMax; i++) {
+        if (i < p && !is_zero_bits(R.res[j][i])) {
+          const ExactProd e = exact_product(R.res[j][i], 1.0);
+          bad |= e.bad;
+          exact_deposit(R.win[j], sacc + j * kNDig * kCopies, copy, e);
+        }
       }
+      window_flush(R.win[j], sacc + j * kNDig * kCopies, copy);
     }
+    if (bad) atomicOr(&ws->flags, 1u);
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, ws->digits[j]);
   } else {
 #pragma unroll
     for (int j = 0; j < NACC; j++) {
@@ -196,27 +180,16 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
       }
     }
   } else if constexpr (V == RPCG_FPE) {
-    const int g = gridDim.x;
     for (int j = 0; j < NACC; j++) {
-      for (int t = threadIdx.x; t < g; t += BLOCK) {
-#pragma unroll
-        for (int i = 0; i < kFpeMax; i++) fs->fpe[t * kFpeMax + i] = __ldcg(&ws->fpe[j][t][i]);
-      }
-      if (threadIdx.x == 0) fs->slost = 0;
-      fpe_tree_pass<BLOCK>(fs->fpe, g, p, &fs->slost);
-      if (threadIdx.x == 0) {
-        bool fin = true;
-        for (int i = 0; i < p; i++) fin &= isfinite(fs->fpe[i]);
-        fs->value[j] = fin ? exact_sum_terms(fs->fpe, p, fs->dig, fs->D) : __longlong_as_double(0x7FF8000000000000ll);
-        fs->lost[j] = (fs->slost || !fin) ? 1 : 0;
-      }
+      const double v = take_and_round(ws->digits[j], fs->dig, fs->D, fs->range);
+      if (threadIdx.x == 0) fs->value[j] = v;
       __syncthreads();
     }
     if (threadIdx.x == 0) {
       const unsigned int f = atomicExch(&ws->flags, 0u);
       for (int j = 0; j < NACC; j++) {
-        fs->lost[j] |= (f & (2u << j)) ? 1 : 0;
-        if (f & 1u) {  // a non-finite operand
+        fs->lost[j] = (f & (2u << j)) ? 1 : 0;
+        if (f & 1u) {  // a non-finite operand (or expansion term)
           fs->lost[j] = 1;
           fs->value[j] = __longlong_as_double(0x7FF8000000000000ll);
         }
@@ -353,7 +326,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_a(MatDev m, const double* __rest
     return;
   }
   const int p = st->fpe_p;
-  if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc);
+  if constexpr (V != RPCG_PLAIN) smem_acc_zero(sacc);
   __syncthreads();
   Reducer<V, 1> R;
   red_init(R);
@@ -395,7 +368,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
   const int p = st->fpe_p;
   double* __restrict__ x = args->x;
   const double rho = st->rho, nrho = -st->rho;
-  if constexpr (V == RPCG_EXBLAS) smem_acc_zero(sacc, 2);
+  if constexpr (V != RPCG_PLAIN) smem_acc_zero(sacc, 2);
   __syncthreads();
   Reducer<V, 2> R;
   red_init(R);
@@ -641,10 +614,6 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
       occ = 1;
   }
   int grid_tiles = grid > 0 ? grid : sms * occ;
-  if (V == RPCG_FPE) {
-    if (grid_stream > 512) grid_stream = 512;
-    if (grid_tiles > 512) grid_tiles = 512;
-  }
   if (grid_stream > kMaxPassGrid) grid_stream = kMaxPassGrid;
   if (grid_tiles > kMaxPassGrid) grid_tiles = kMaxPassGrid;
   if (grid_tiles > ntiles) grid_tiles = ntiles > 0 ? ntiles : 1;  // ntiles: CTAs of BLOCK rows
@@ -1165,7 +1134,6 @@ static rpcg_status solve_impl(rpcg_matrix_t A, const double* b, double* x, int32
   RPCG_CHECK_ARG(opt.grid >= 0 && opt.grid <= kMaxPassGrid, "grid must be 0..4096");
   const int block = pick_block(opt.block);
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == block, "block must be 0, 128, 256 or 512");
-  if (v == RPCG_FPE && opt.grid > 512) opt.grid = 512;
   const int n = A->m.n;
   if (n == 0 && async) {
     // nothing to solve: the result of an empty system, written in stream order
