@@ -125,7 +125,7 @@ def small_system_rates(P, dev, stream, steps=20):
     b = M.spmv(torch.from_numpy(xt).to(dev))
     x = torch.zeros(A.n, dtype=torch.float64, device=dev)
     out = {}
-    for v, k in (("exblas", steps), ("plain", steps), ("fpe", 3)):
+    for v, k in (("exblas", steps), ("plain", steps), ("fpe", steps)):
         for _ in range(3):
             x.zero_()
             r = M.solve(b, x, variant=v, tol=1e-8, max_iter=1000)
@@ -142,6 +142,7 @@ def small_system_rates(P, dev, stream, steps=20):
         out[v] = {"iters_per_s": it / (e0.elapsed_time(e1) / 1e3), "iterations": r["iterations"],
                   "status": r["status"], "path": M.solve_path(v)}
     out["overhead_exblas_vs_plain"] = out["plain"]["iters_per_s"] / out["exblas"]["iters_per_s"]
+    out["overhead_fpe_vs_plain"] = out["plain"]["iters_per_s"] / out["fpe"]["iters_per_s"]
     out["workload"] = "poisson7_16 (n 4096, nnz 27136), b = A x_true, tol 1e-8, complete solves from x0 = 0"
     return out
 

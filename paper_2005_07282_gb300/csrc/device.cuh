@@ -482,11 +482,18 @@ __device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, do
 }
 
 // Alg. 3: a += b; returns true if a term was lost.
+// The loop over b's terms is rolled (the term is picked by selects, so both
+// expansions stay in registers): one copy of Alg. 4's loop instead of
+// kFpeMax keeps the code small.
 __device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[kFpeMax], int p) {
   bool lost = false;
+#pragma unroll 1
+  for (int i = 0; i < p; i++) {
+    double bi = b[0];
 #pragma unroll
-  for (int i = 0; i < kFpeMax; i++) {
-    if (i < p && !is_zero_bits(b[i])) lost |= !is_zero_bits(fpe_accumulate(a, p, b[i]));
+    for (int k = 1; k < kFpeMax; k++)
+      if (i == k) bi = b[k];
+    if (!is_zero_bits(bi)) lost |= !is_zero_bits(fpe_accumulate(a, p, bi));
   }
   return lost;
 }

@@ -44,8 +44,11 @@ def _same(ra, xa, rs, xs):
     ("p27_30", "exblas", {}, "graph"),                 # 27000 rows: beyond the cluster path
     ("p7_16", "exblas", {"block": 256}, "graph"),
     ("p7_16", "plain", {}, "cluster"),
-    ("p7_9", "fpe", {}, "graph"),
-    ("p7_9", "fpe", {"fpe_size": 2, "fpe_strict": 1}, "graph"),
+    ("p7_9", "fpe", {}, "cluster"),
+    ("p7_9", "fpe", {"fpe_size": 2, "fpe_strict": 1}, "cluster"),
+    ("p7_9", "fpe", {"fpe_size": 1}, "cluster"),
+    ("p7_9", "fpe", {"block": 256}, "graph"),
+    ("p7_9", "fpe", {"fpe_size": 2, "fpe_strict": 1, "block": 128}, "graph"),
 ])
 def test_async_equals_sync(rpcg, cuda, oracle_lib, kind, variant, kw, path):
     import torch

@@ -60,7 +60,8 @@ def test_cluster_equals_graph_and_oracle(rpcg, cuda, oracle_lib, kind):
     M = rpcg.Matrix.from_csr(A)
     assert M.solve_path("exblas") == "cluster"
     assert M.solve_path("exblas", block=256) == "graph"
-    assert M.solve_path("fpe") == "graph"
+    assert M.solve_path("fpe") == "cluster"
+    assert M.solve_path("fpe", grid=4) == "graph"
     kw = dict(tol=1e-10, max_iter=3000)
     rc, xc, hc = _solve(M, b, cuda, "exblas", **kw)
     rg, xg, hg = _solve(M, b, cuda, "exblas", block=256, **kw)
@@ -93,9 +94,58 @@ def test_cluster_nonzero_x0_host_api_and_fpe(rpcg, cuda, oracle_lib):
     xh = x0.copy()
     rh = M.solve_host(b, xh, variant="exblas", tol=1e-9, max_iter=3000)
     assert rh["iterations"] == ref["iterations"] and np.array_equal(bits(xh), bits(ref["x"]))
-    # fpe (graph path, exact recompute on inexact dots) lands on the same bits
+    # fpe (exact recompute on inexact dots) lands on the same bits, on both paths
     rf, xf, _ = _solve(M, b, cuda, "fpe", x0=x0, tol=1e-9, max_iter=3000)
     assert rf["iterations"] == ref["iterations"] and np.array_equal(bits(xf), bits(ref["x"]))
+    rg, xg, _ = _solve(M, b, cuda, "fpe", x0=x0, block=256, tol=1e-9, max_iter=3000)
+    assert rg["iterations"] == ref["iterations"] and np.array_equal(bits(xg), bits(ref["x"]))
+
+
+@pytest.mark.parametrize("kind", ["p7_16", "p27_10", "diff_9", "p7_25", "band"])
+@pytest.mark.parametrize("fpe_size", [1, 2, 8, 0])
+def test_cluster_fpe_follows_the_exact_trajectory(rpcg, cuda, oracle_lib, kind, fpe_size):
+    """The fpe variant on the cluster path: per-thread expansions of Algs. 2-4
+    whose terms meet exactly in the long accumulator; a dot whose expansions
+    lost bits is recomputed exactly, so every size (and the adaptive one,
+    fpe_size = 0) follows the oracle's exact-dot trajectory bit for bit."""
+    A = _system(kind)
+    b = oracle_lib.spmv(A, synth.poisson_rhs_xtrue(A.n, SEED + 21))
+    M = rpcg.Matrix.from_csr(A)
+    assert M.solve_path("fpe") == "cluster"
+    kw = dict(tol=1e-10, max_iter=3000)
+    r, x, h = _solve(M, b, cuda, "fpe", fpe_size=fpe_size, **kw)
+    ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, nthreads=4, **kw)
+    assert r["status"] == ref["status"] == 0
+    assert r["iterations"] == ref["iterations"]
+    assert np.array_equal(bits(x), bits(ref["x"])) and np.array_equal(bits(h), bits(ref["history"]))
+    assert bits([r["relres"]])[0] == bits([ref["relres"]])[0]
+    if fpe_size == 1:  # one term cannot hold a product's rounding error
+        assert r["fpe_inexact_count"] > 0 and r["fpe_size_used"] == 1
+    elif fpe_size == 0:
+        n = r["fpe_inexact_count"]  # each phase that saw an inexact dot adds one term
+        assert r["fpe_size_used"] == 3 if n == 0 else 3 < r["fpe_size_used"] <= min(8, 3 + n)
+    else:
+        assert r["fpe_size_used"] == fpe_size
+
+
+def test_cluster_fpe_strict(rpcg, cuda, oracle_lib):
+    """fpe_strict = 1: inexact dots are reported, not recomputed.  With 8
+    terms nothing is lost on the 16^3 system and the result is the exact
+    trajectory; with one term the solve still converges and reports
+    RPCG_FPE_INEXACT with the count, as the multi-pass path does."""
+    A = _system("p7_16")
+    b = oracle_lib.spmv(A, synth.poisson_rhs_xtrue(A.n, SEED + 22))
+    M = rpcg.Matrix.from_csr(A)
+    kw = dict(tol=1e-10, max_iter=3000)
+    ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, nthreads=4, **kw)
+    r8, x8, _ = _solve(M, b, cuda, "fpe", fpe_size=8, fpe_strict=1, **kw)
+    assert r8["status"] == 0 and r8["fpe_inexact_count"] == 0
+    assert r8["iterations"] == ref["iterations"] and np.array_equal(bits(x8), bits(ref["x"]))
+    r1, x1, _ = _solve(M, b, cuda, "fpe", fpe_size=1, fpe_strict=1, **kw)
+    assert r1["status"] == rpcg.FPE_INEXACT and r1["fpe_inexact_count"] > 0
+    assert r1["relres"] < 1e-10 and abs(r1["iterations"] - ref["iterations"]) <= 3
+    g1, _, _ = _solve(M, b, cuda, "fpe", fpe_size=1, fpe_strict=1, block=256, **kw)
+    assert g1["status"] == rpcg.FPE_INEXACT and g1["fpe_inexact_count"] > 0
 
 
 def _edge_cases():
@@ -119,13 +169,14 @@ def _edge_cases():
     ]
 
 
+@pytest.mark.parametrize("variant", ["exblas", "fpe"])
 @pytest.mark.parametrize("case", range(9))
-def test_cluster_edge_cases_match_graph_and_oracle(rpcg, cuda, oracle_lib, case):
+def test_cluster_edge_cases_match_graph_and_oracle(rpcg, cuda, oracle_lib, case, variant):
     name, A, b, x0, kw = _edge_cases()[case]
     M = rpcg.Matrix.from_csr(A)
-    assert M.solve_path("exblas") == "cluster"
-    rc, xc, hc = _solve(M, b, cuda, "exblas", x0=x0, **kw)
-    rg, xg, hg = _solve(M, b, cuda, "exblas", x0=x0, block=128, **kw)
+    assert M.solve_path(variant) == "cluster"
+    rc, xc, hc = _solve(M, b, cuda, variant, x0=x0, **kw)
+    rg, xg, hg = _solve(M, b, cuda, variant, x0=x0, block=128, **kw)
     assert rc["status"] == rg["status"], name
     assert rc["iterations"] == rg["iterations"], name
     assert np.array_equal(bits(xc), bits(xg)), name
