@@ -492,8 +492,9 @@ def dot_arm(args):
 
 
 def batch_arm(args):
-    """--batch COUNT: one batched solve of COUNT systems per step (exblas,
-    tol 1e-10), against solving the same systems one after the other."""
+    """--batch COUNT: one batched solve of COUNT systems per step (--variant,
+    exblas by default; tol 1e-10), against solving the same systems one after
+    the other."""
     import torch
 
     import paper_2005_07282_gb300 as P
@@ -509,14 +510,14 @@ def batch_arm(args):
     opts = dict(tol=1e-10, max_iter=args.max_iter)
     Bt = P.Batch(Ms)
     if args.eager:
-        Bt.solve(bs, xs, variant="exblas", **opts)  # autotune once (graph form), then time pass by pass
+        Bt.solve(bs, xs, variant=args.variant, **opts)  # autotune once (graph form), then time pass by pass
 
     def run():
         for x in xs:
             x.zero_()
         if args.eager:  # kernel by kernel (profilers see every launch)
-            return Bt.solve_profiled(bs, xs, variant="exblas", **opts)[0]
-        return Bt.solve(bs, xs, variant="exblas", **opts)
+            return Bt.solve_profiled(bs, xs, variant=args.variant, **opts)[0]
+        return Bt.solve(bs, xs, variant=args.variant, **opts)
 
     for _ in range(args.warmup):
         res = run()
@@ -535,7 +536,7 @@ def batch_arm(args):
         x.zero_()
     torch.cuda.synchronize()
     e0.record()
-    solo = [M.solve(b, x, variant="exblas", **opts) for M, b, x in zip(Ms, bs, xs)]
+    solo = [M.solve(b, x, variant=args.variant, **opts) for M, b, x in zip(Ms, bs, xs)]
     e1.record()
     torch.cuda.synchronize()
     solo_ms = e0.elapsed_time(e1)
@@ -546,12 +547,12 @@ def batch_arm(args):
     blk, tile = Bt.tuned()
     for x in xs:
         x.zero_()
-    _, pass_ms, pass_launches = Bt.solve_profiled(bs, xs, variant="exblas", **opts)
+    _, pass_ms, pass_launches = Bt.solve_profiled(bs, xs, variant=args.variant, **opts)
     moved = sum(r["iterations"] * iter_bytes(A.n, A.nnz) for r, A in zip(res, mats))
     # rows still iterating at every 40th iteration (the shrinking active set)
     active_rows = {k: sum(A.n for r, A in zip(res, mats) if r["iterations"] > k) for k in range(0, max(its), 40)}
     peak, peak_kind = hbm_peak()
-    print(json.dumps({"workload": f"batch of {args.batch} diffusion7 systems, s~U{{8..64}}, tol 1e-10, exblas",
+    print(json.dumps({"workload": f"batch of {args.batch} diffusion7 systems, s~U{{8..64}}, tol 1e-10, {args.variant}",
                       "rows": rows, "nnz": nnz, "solves_per_s": args.batch / (ms / 1e3), "ms_per_batch": ms,
                       "iterations": {"total": sum(its), "min": min(its), "max": max(its),
                                      "mean": sum(its) / len(its)},

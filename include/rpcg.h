@@ -211,7 +211,7 @@ rpcg_status rpcg_dot_plain(int64_t n, const double *a, const double *b, double *
  * tau0 = <r0,r0>, ||b|| = RN(sqrt(<b,b>)).  The loop runs on the device
  * while relres >= tol and iterations < max_iter: as a CUDA graph of
  * grid-wide passes with a conditional while node, or, for systems of up to
- * 16384 rows whose slabs fit shared memory (plain and exblas variants, o->block
+ * 16384 rows whose slabs fit shared memory (every variant, o->block
  * and o->grid 0), as one launch of a thread-block cluster of up to 16 CTAs
  * that keeps the matrix and vectors in shared memory (rpcg_solve_path).
  * With RPCG_EXBLAS, and RPCG_FPE with fpe_strict = 0, every iterate,
@@ -284,8 +284,11 @@ rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double *b_host, double *x_hos
  * when it stops.
  *   b, x      host arrays of `count` device pointers (b[i], x[i]: n_i doubles;
  *             x[i] in = x0, out = the iterate).
- *   v         RPCG_EXBLAS (bit-identical to rpcg_solve of each system alone)
- *             or RPCG_PLAIN.
+ *   v         RPCG_EXBLAS or RPCG_FPE with fpe_strict = 0 (bit-identical to
+ *             rpcg_solve of each system alone; a system whose FPE dots lost
+ *             bits recomputes them exactly, the others skip that pass),
+ *             RPCG_FPE with fpe_strict = 1 (inexact dots counted, status
+ *             RPCG_FPE_INEXACT), or RPCG_PLAIN.
  *   o         options; o->history, if set, is a device array of
  *             count x (max_iter + 1) doubles (row i for system i).
  *             o->block (0, 128, 256) and o->tile (0 or rows per unit): a zero

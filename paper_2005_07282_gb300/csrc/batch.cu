@@ -16,8 +16,10 @@
 // Every row, element and scalar operation is the one rpcg_solve performs
 // and exact dots do not depend on how the work is split, so each system's
 // iterates, residuals and iteration count are bit-identical to solving it
-// alone (with RPCG_EXBLAS).  The plain variant sums unit partials in unit
-// order: deterministic for a given tile size, not reproducible across tiles.
+// alone (with RPCG_EXBLAS, and with RPCG_FPE, whose inexact dots are
+// recomputed exactly by two extra passes that skip the other systems).  The
+// plain variant sums unit partials in unit order: deterministic for a given
+// tile size, not reproducible across tiles.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -94,17 +96,26 @@ static cudaError_t add_node(cudaGraph_t g, cudaGraphNode_t* node, const cudaGrap
 // Grid sizes and dynamic shared memory of the batch kernels for one
 // (variant, block, tile): persistent grids of the occupancy limit.
 struct BatchPlan {
-  int g_setup, g_a, g_b, g_c, g_q;
-  size_t sm1, sm2, sm3;
+  int g_setup, g_a, g_b, g_c, g_q, g_ra, g_rb;
+  size_t sm1, sm2, sm3, smr1, smr2;
 };
+
+// the set-up dots of the fpe variant are exact (the single-system rule)
+template <int V>
+constexpr int setup_variant() {
+  return V == RPCG_FPE ? RPCG_EXBLAS : V;
+}
 
 template <int V, int BLOCK>
 static rpcg_status batch_plan(rpcg_batch_t B, const rpcg_batch_s::Layout* L, BatchPlan* P) {
   const int count = B->count;
+  constexpr int VS = setup_variant<V>();
   P->sm1 = b_smem<V>(1, count);
   P->sm2 = b_smem<V>(2, count);
-  P->sm3 = b_smem<V>(3, count);
-  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_setup<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm3));
+  P->sm3 = b_smem<VS>(3, count);
+  P->smr1 = b_smem<RPCG_EXBLAS>(1, count);
+  P->smr2 = b_smem<RPCG_EXBLAS>(2, count);
+  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_setup<VS, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm3));
   RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_a<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm1));
   RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm2));
   auto occ_grid = [&](const void* f, size_t smem) {
@@ -114,11 +125,18 @@ static rpcg_status batch_plan(rpcg_batch_t B, const rpcg_batch_s::Layout* L, Bat
     if (g > L->total) g = L->total > 0 ? L->total : 1;
     return g;
   };
-  P->g_setup = occ_grid((const void*)k_b_setup<V, BLOCK>, P->sm3);
+  P->g_setup = occ_grid((const void*)k_b_setup<VS, BLOCK>, P->sm3);
   P->g_a = occ_grid((const void*)k_b_pass_a<V, BLOCK>, P->sm1);
   P->g_b = occ_grid((const void*)k_b_pass_b<V, BLOCK>, P->sm2);
   P->g_c = occ_grid((const void*)k_b_pass_c<BLOCK>, 0);
   P->g_q = occ_grid((const void*)k_b_inv_q, 0);
+  P->g_ra = P->g_rb = 1;
+  if constexpr (V == RPCG_FPE) {
+    RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_redo_a<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smr1));
+    RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_redo_b<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smr2));
+    P->g_ra = occ_grid((const void*)k_b_redo_a<BLOCK>, P->smr1);
+    P->g_rb = occ_grid((const void*)k_b_redo_b<BLOCK>, P->smr2);
+  }
   return RPCG_OK;
 }
 
@@ -133,6 +151,7 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
   const int count = B->count;
   const int g_setup = P.g_setup, g_a = P.g_a, g_b = P.g_b, g_c = P.g_c, g_q = P.g_q;
   const size_t sm1 = P.sm1, sm2 = P.sm2, sm3 = P.sm3;
+  constexpr int VS = setup_variant<V>();
 
   cudaGraph_t g = nullptr;
   RPCG_CUDA_TRY(cudaGraphCreate(&g, 0));
@@ -148,7 +167,7 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
   {
     void* a[] = {&D, &aprefix};
     RPCG_CUDA_TRY(add_node(g, &n_q, &n_init, 1, (const void*)k_b_inv_q, g_q, BLOCK, 0, a));
-    RPCG_CUDA_TRY(add_node(g, &n_setup, &n_q, 1, (const void*)k_b_setup<V, BLOCK>, g_setup, BLOCK, sm3, a));
+    RPCG_CUDA_TRY(add_node(g, &n_setup, &n_q, 1, (const void*)k_b_setup<VS, BLOCK>, g_setup, BLOCK, sm3, a));
   }
   {
     void* a[] = {&D, &cond};
@@ -165,7 +184,17 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
   {
     void* a[] = {&D};
     RPCG_CUDA_TRY(add_node(body, &b_a, nullptr, 0, (const void*)k_b_pass_a<V, BLOCK>, g_a, BLOCK, sm1, a));
+    if constexpr (V == RPCG_FPE) {  // the exact recomputations follow their passes
+      cudaGraphNode_t b_ra;
+      RPCG_CUDA_TRY(add_node(body, &b_ra, &b_a, 1, (const void*)k_b_redo_a<BLOCK>, P.g_ra, BLOCK, P.smr1, a));
+      b_a = b_ra;
+    }
     RPCG_CUDA_TRY(add_node(body, &b_b, &b_a, 1, (const void*)k_b_pass_b<V, BLOCK>, g_b, BLOCK, sm2, a));
+    if constexpr (V == RPCG_FPE) {
+      cudaGraphNode_t b_rb;
+      RPCG_CUDA_TRY(add_node(body, &b_rb, &b_b, 1, (const void*)k_b_redo_b<BLOCK>, P.g_rb, BLOCK, P.smr2, a));
+      b_b = b_rb;
+    }
     RPCG_CUDA_TRY(add_node(body, &b_c, &b_b, 1, (const void*)k_b_pass_c<BLOCK>, g_c, BLOCK, 0, a));
   }
   {
@@ -189,8 +218,15 @@ static rpcg_status batch_get_graph(rpcg_batch_t B, int v, int block, int tile, c
   cudaGraph_t g = nullptr;
   cudaGraphExec_t ex = nullptr;
   rpcg_status st;
-  if (block == 128) st = v == RPCG_PLAIN ? batch_graph<RPCG_PLAIN, 128>(B, tile, &g, &ex) : batch_graph<RPCG_EXBLAS, 128>(B, tile, &g, &ex);
-  else st = v == RPCG_PLAIN ? batch_graph<RPCG_PLAIN, 256>(B, tile, &g, &ex) : batch_graph<RPCG_EXBLAS, 256>(B, tile, &g, &ex);
+  if (block == 128) {
+    if (v == RPCG_PLAIN) st = batch_graph<RPCG_PLAIN, 128>(B, tile, &g, &ex);
+    else if (v == RPCG_FPE) st = batch_graph<RPCG_FPE, 128>(B, tile, &g, &ex);
+    else st = batch_graph<RPCG_EXBLAS, 128>(B, tile, &g, &ex);
+  } else {
+    if (v == RPCG_PLAIN) st = batch_graph<RPCG_PLAIN, 256>(B, tile, &g, &ex);
+    else if (v == RPCG_FPE) st = batch_graph<RPCG_FPE, 256>(B, tile, &g, &ex);
+    else st = batch_graph<RPCG_EXBLAS, 256>(B, tile, &g, &ex);
+  }
   if (st != RPCG_OK) {
     if (g) cudaGraphDestroy(g);
     return st;
@@ -225,7 +261,8 @@ static void batch_upload(rpcg_batch_t B, const double* const* b, double* const* 
   for (int i = 0; i < B->count; i++) {
     rpcg_matrix_t A = B->mats[i];
     double* hist = o.history ? o.history + (size_t)i * (o.max_iter + 1) : nullptr;
-    B->h_sys[i] = SysDev{A->m, b[i], x[i], A->r, A->d, A->w, A->inv, hist, o.tol, o.max_iter, 0};
+    B->h_sys[i] = SysDev{A->m, b[i], x[i], A->r, A->d, A->w, A->inv, hist, o.tol, o.max_iter, o.fpe_size,
+                         o.fpe_strict ? 1 : 0, 0};
   }
 }
 
@@ -250,7 +287,7 @@ static rpcg_status batch_run(rpcg_batch_t B, const double* const* b, double* con
 // batch_results): NOT_CONVERGED when a system stopped at max_iter, x = 0
 // for b = 0, an empty system OK with nothing done.  One block per system.
 static __global__ void k_b_results(const SysDev* __restrict__ sys, const SysState* __restrict__ st, int count,
-                                   rpcg_result* out) {
+                                   int variant, rpcg_result* out) {
   for (int s = blockIdx.x; s < count; s += gridDim.x) {
     const SysState t = st[s];
     const int n = sys[s].m.n;
@@ -260,11 +297,16 @@ static __global__ void k_b_results(const SysDev* __restrict__ sys, const SysStat
       rpcg_result r{0, RPCG_OK, 0.0, 0.0, 0, 0};
       if (n > 0) {
         int status = t.status;
-        if (status == RPCG_OK && !(t.rel < sys[s].tol)) status = RPCG_NOT_CONVERGED;
+        if (status == RPCG_OK) {
+          if (!(t.rel < sys[s].tol)) status = RPCG_NOT_CONVERGED;
+          else if (variant == RPCG_FPE && sys[s].fpe_strict && t.fpe_inexact > 0) status = RPCG_FPE_INEXACT;
+        }
         r.iterations = t.iter;
         r.status = status;
         r.relres = t.rel;
         r.tau = t.tau;
+        r.fpe_inexact_count = t.fpe_inexact;
+        r.fpe_size_used = variant == RPCG_FPE ? t.fpe_p : 0;
       }
       out[s] = r;
     }
@@ -307,15 +349,23 @@ static rpcg_status batch_eager(rpcg_batch_t B, int tile, cudaStream_t s, float* 
     return err == cudaSuccess ? *h_active : 0;
   };
   const int* ap = B->d_aprefix;
+  constexpr int VS = setup_variant<V>();
   timed(0, 3, [&] {
     k_b_init<<<1, 256, 0, s>>>(D);
     k_b_inv_q<<<P.g_q, BLOCK, 0, s>>>(D, ap);
-    k_b_setup<V, BLOCK><<<P.g_setup, BLOCK, P.sm3, s>>>(D, ap);
+    k_b_setup<VS, BLOCK><<<P.g_setup, BLOCK, P.sm3, s>>>(D, ap);
   });
   timed(4, 1, [&] { k_b_retire<<<1, 256, 0, s>>>(D); });
   while (active() > 0) {
-    timed(1, 1, [&] { k_b_pass_a<V, BLOCK><<<P.g_a, BLOCK, P.sm1, s>>>(D); });
-    timed(2, 1, [&] { k_b_pass_b<V, BLOCK><<<P.g_b, BLOCK, P.sm2, s>>>(D); });
+    // the fpe variant's exact recomputations count with their passes
+    timed(1, 1, [&] {
+      k_b_pass_a<V, BLOCK><<<P.g_a, BLOCK, P.sm1, s>>>(D);
+      if (V == RPCG_FPE) k_b_redo_a<BLOCK><<<P.g_ra, BLOCK, P.smr1, s>>>(D);
+    });
+    timed(2, 1, [&] {
+      k_b_pass_b<V, BLOCK><<<P.g_b, BLOCK, P.sm2, s>>>(D);
+      if (V == RPCG_FPE) k_b_redo_b<BLOCK><<<P.g_rb, BLOCK, P.smr2, s>>>(D);
+    });
     timed(3, 1, [&] { k_b_pass_c<BLOCK><<<P.g_c, BLOCK, 0, s>>>(D); });
     timed(4, 1, [&] { k_b_retire<<<1, 256, 0, s>>>(D); });
   }
@@ -330,7 +380,7 @@ static rpcg_status batch_eager(rpcg_batch_t B, int tile, cudaStream_t s, float* 
 }
 
 // Read the per-system states after a run and fill `res`; returns the worst status.
-static rpcg_status batch_results(rpcg_batch_t B, double* const* x, const rpcg_opts& opt, rpcg_result* res,
+static rpcg_status batch_results(rpcg_batch_t B, double* const* x, int v, const rpcg_opts& opt, rpcg_result* res,
                                  cudaStream_t s) {
   RPCG_CUDA_TRY(cudaMemcpyAsync(B->h_state, B->d_state, B->count * sizeof(SysState), cudaMemcpyDeviceToHost, s));
   RPCG_CUDA_TRY(cudaStreamSynchronize(s));
@@ -344,8 +394,11 @@ static rpcg_status batch_results(rpcg_batch_t B, double* const* x, const rpcg_op
     }
     if (h.bzero) RPCG_CUDA_TRY(cudaMemsetAsync(x[i], 0, (size_t)n * sizeof(double), s));
     int status = h.status;
-    if (status == RPCG_OK && !(h.rel < opt.tol)) status = RPCG_NOT_CONVERGED;
-    res[i] = rpcg_result{h.iter, status, h.rel, h.tau, 0, 0};
+    if (status == RPCG_OK) {
+      if (!(h.rel < opt.tol)) status = RPCG_NOT_CONVERGED;
+      else if (v == RPCG_FPE && opt.fpe_strict && h.fpe_inexact > 0) status = RPCG_FPE_INEXACT;
+    }
+    res[i] = rpcg_result{h.iter, status, h.rel, h.tau, h.fpe_inexact, v == RPCG_FPE ? h.fpe_p : 0};
     if (status < 0 && (worst >= 0 || status < worst)) worst = (rpcg_status)status;
     else if (status > 0 && worst == RPCG_OK) worst = (rpcg_status)status;
   }
@@ -402,11 +455,12 @@ rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double* const* b, double* con
                              rpcg_result* res, void* stream) {
   clear_error();
   RPCG_CHECK_ARG(B != nullptr && b != nullptr && x != nullptr && res != nullptr, "NULL argument");
-  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS, "batched solves support the plain and exblas variants");
+  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS || v == RPCG_FPE, "unknown variant");
   rpcg_opts opt;
   if (o) opt = *o;
   else rpcg_opts_default(&opt);
   RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
+  RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
   RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
   for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
@@ -456,7 +510,7 @@ rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double* const* b, double* con
   }
   rpcg_status st = batch_run(B, b, x, v, opt, block, tile, s);
   if (st != RPCG_OK) return st;
-  return batch_results(B, x, opt, res, s);
+  return batch_results(B, x, v, opt, res, s);
 }
 
 rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double* const* b, double* const* x, int32_t v,
@@ -465,11 +519,12 @@ rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double* const* b, do
   clear_error();
   RPCG_CHECK_ARG(B != nullptr && b != nullptr && x != nullptr && res != nullptr && pass_ms != nullptr,
                  "NULL argument");
-  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS, "batched solves support the plain and exblas variants");
+  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS || v == RPCG_FPE, "unknown variant");
   rpcg_opts opt;
   if (o) opt = *o;
   else rpcg_opts_default(&opt);
   RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
+  RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
   RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
   for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
@@ -482,25 +537,29 @@ rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double* const* b, do
   batch_upload(B, b, x, opt);
   RPCG_CUDA_TRY(cudaMemcpyAsync(B->d_sys, B->h_sys, B->count * sizeof(SysDev), cudaMemcpyHostToDevice, s));
   rpcg_status st;
-  if (block == 128)
-    st = v == RPCG_PLAIN ? batch_eager<RPCG_PLAIN, 128>(B, tile, s, pass_ms, launches)
-                         : batch_eager<RPCG_EXBLAS, 128>(B, tile, s, pass_ms, launches);
-  else
-    st = v == RPCG_PLAIN ? batch_eager<RPCG_PLAIN, 256>(B, tile, s, pass_ms, launches)
-                         : batch_eager<RPCG_EXBLAS, 256>(B, tile, s, pass_ms, launches);
+  if (block == 128) {
+    if (v == RPCG_PLAIN) st = batch_eager<RPCG_PLAIN, 128>(B, tile, s, pass_ms, launches);
+    else if (v == RPCG_FPE) st = batch_eager<RPCG_FPE, 128>(B, tile, s, pass_ms, launches);
+    else st = batch_eager<RPCG_EXBLAS, 128>(B, tile, s, pass_ms, launches);
+  } else {
+    if (v == RPCG_PLAIN) st = batch_eager<RPCG_PLAIN, 256>(B, tile, s, pass_ms, launches);
+    else if (v == RPCG_FPE) st = batch_eager<RPCG_FPE, 256>(B, tile, s, pass_ms, launches);
+    else st = batch_eager<RPCG_EXBLAS, 256>(B, tile, s, pass_ms, launches);
+  }
   if (st != RPCG_OK) return st;
-  return batch_results(B, x, opt, res, s);
+  return batch_results(B, x, v, opt, res, s);
 }
 
 rpcg_status rpcg_batch_solve_async(rpcg_batch_t B, const double* const* b, double* const* x, int32_t v,
                                    const rpcg_opts* o, rpcg_result* res, void* stream) {
   clear_error();
   RPCG_CHECK_ARG(B != nullptr && b != nullptr && x != nullptr && res != nullptr, "NULL argument");
-  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS, "batched solves support the plain and exblas variants");
+  RPCG_CHECK_ARG(v == RPCG_PLAIN || v == RPCG_EXBLAS || v == RPCG_FPE, "unknown variant");
   rpcg_opts opt;
   if (o) opt = *o;
   else rpcg_opts_default(&opt);
   RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
+  RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
   RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
   for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
@@ -510,7 +569,7 @@ rpcg_status rpcg_batch_solve_async(rpcg_batch_t B, const double* const* b, doubl
   const int tile = opt.tile ? opt.tile : (B->tuned_tile ? B->tuned_tile : 1024);
   rpcg_status st = batch_run(B, b, x, v, opt, block, tile, s);
   if (st != RPCG_OK) return st;
-  k_b_results<<<std::max(1, std::min(B->count, sm_count() * 8)), 256, 0, s>>>(B->d_sys, B->d_state, B->count, res);
+  k_b_results<<<std::max(1, std::min(B->count, sm_count() * 8)), 256, 0, s>>>(B->d_sys, B->d_state, B->count, v, res);
   RPCG_CUDA_TRY(cudaGetLastError());
   return RPCG_OK;
 }

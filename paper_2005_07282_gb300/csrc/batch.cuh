@@ -32,12 +32,15 @@ struct SysDev {
   double* history;  // max_iter + 1 relres values, or null
   double tol;
   int max_iter;
+  int fpe_size, fpe_strict;  // fpe variant: expansion size (0: adaptive), 1: report inexact dots
   int pad;
 };
 
 struct SysState {
   double rho, beta, beta_old, tau, gamma, bnorm, rel;
   int iter, status, bad_row, bzero, active, pad;
+  int fpe_p, fpe_inexact;  // fpe variant: expansion size in use, inexact dots seen
+  int redo, pad2;          // fpe variant: 1 / 2 = pass A's / pass B's dots to recompute exactly
 };
 
 // per-system reduction scratch (digits, arrival counter, flags)
@@ -48,12 +51,12 @@ struct SysRed {
 };
 
 constexpr int kChunkUnits = 4;  // listed units a CTA takes at a time
-enum { kWorkSetup = 0, kWorkA = 1, kWorkB = 2 };
+enum { kWorkSetup = 0, kWorkA = 1, kWorkB = 2, kWorkRA = 3, kWorkRB = 4, kWorkCounters = 6 };
 
 struct BatchHead {
   int active_count;  // systems still iterating
-  int pad;
-  unsigned int work[4];  // work counters of the reducing passes
+  int redo_any;      // fpe variant: bit 0 / 1 = some system recomputes pass A's / pass B's dots
+  unsigned int work[kWorkCounters];  // work counters of the reducing passes
 };
 
 // Everything the kernels need about a batch (passed by value).
@@ -170,6 +173,7 @@ struct UnitSmem {
   double value[3];
   int range[2];
   int base;
+  unsigned int lost;  // fpe: bit j = dot j inexact (an expansion lost bits, or a non-finite operand)
   bool last;
 };
 
@@ -179,24 +183,30 @@ constexpr int kPrefixSmem = 1024;
 
 template <int V>
 __host__ __device__ constexpr size_t b_smem(int nacc, int count) {
-  return (V == RPCG_EXBLAS ? (size_t)nacc * kNDig * kCopies * 8 : 0) + sizeof(UnitSmem) +
+  return (V != RPCG_PLAIN ? (size_t)nacc * kNDig * kCopies * 8 : 0) + sizeof(UnitSmem) +
          (size_t)(count + 1 <= kPrefixSmem ? count + 1 : 0) * 4 + 16;
 }
 
 // Process the listed units of `prefix`, taking chunks from *work.
-// row_fn(sys, row, dep) deposits dep(j, a, b) into dot j; fin_fn(sys, values)
-// runs in thread 0 of the CTA that completes a system.
+// row_fn(sys, row, dep) deposits dep(j, a, b) into dot j; fin_fn(sys,
+// values, lost) runs in thread 0 of the CTA that completes a system (lost:
+// the fpe variant's inexact-dot bits, 0 otherwise).
 // row2_fn(ctx, ra, rb, dep) does rows ra and rb together (both in range);
-// pass a null_row2 to process rows one at a time.
+// pass a NullRow2 to process rows one at a time.  skip_fn(sys) == true
+// skips a system's units altogether (no deposit, no arrival, no fin_fn).
 struct NullRow2 {};
+struct NoSkip {
+  __device__ bool operator()(int) const { return false; }
+};
 
-template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn, class Row2Fn = NullRow2>
+template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn, class Row2Fn = NullRow2,
+          class SkipFn = NoSkip>
 __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restrict__ prefix, unsigned int* work,
                                           unsigned char* smem, CtxFn ctx_fn, PfFn pf_fn, RowFn row_fn,
-                                          FinFn fin_fn, Row2Fn row2_fn = NullRow2{}) {
+                                          FinFn fin_fn, Row2Fn row2_fn = NullRow2{}, SkipFn skip_fn = NoSkip{}) {
   constexpr bool kPair = !std::is_same<Row2Fn, NullRow2>::value;
   unsigned long long* sacc = reinterpret_cast<unsigned long long*>(smem);
-  UnitSmem* us = reinterpret_cast<UnitSmem*>(smem + (V == RPCG_EXBLAS ? NACC * kNDig * kCopies * 8 : 0));
+  UnitSmem* us = reinterpret_cast<UnitSmem*>(smem + (V != RPCG_PLAIN ? NACC * kNDig * kCopies * 8 : 0));
   const int copy = threadIdx.x & (kCopies - 1);
   const int* sp = prefix;
   if (B.count + 1 <= kPrefixSmem) {
@@ -219,6 +229,10 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
     for (int a = base; a < end;) {
       const int s = unit_system(sp, B.count, a);
       const int run_end = min(end, sp[s + 1]);
+      if (skip_fn(s)) {  // the same answer in every thread: a system's record is stable during the pass
+        a = run_end;
+        continue;
+      }
       const int k0 = a - sp[s], k1 = k0 + (run_end - a);  // units [k0, k1) of system s
       const int n = B.sys[s].m.n;
       SysRed* R = B.red + s;
@@ -255,6 +269,62 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         __syncthreads();
 #pragma unroll
         for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, R->digits[j]);
+      } else if constexpr (V == RPCG_FPE) {
+        // each thread's rows into its result and error expansions (Algs. 2
+        // and 4), merged (Alg. 3) at the end of the run; the terms are then
+        // deposited exactly into the system's long accumulator, as in the
+        // single-system passes
+        double res[NACC][kFpeMax], err[NACC][kFpeMax];
+        bool lost[NACC];
+        bool bad = false;
+#pragma unroll
+        for (int j = 0; j < NACC; j++) {
+#pragma unroll
+          for (int i = 0; i < kFpeMax; i++) res[j][i] = err[j][i] = 0.0;
+          lost[j] = false;
+        }
+        const int p = B.st[s].fpe_p;
+        smem_acc_zero(sacc, NACC);
+        __syncthreads();
+        const int r0 = k0 * B.tile, r1 = min(n, k1 * B.tile);
+        auto dep = [&](int j, double x, double y) {
+          if (!is_finite_bits(x) || !is_finite_bits(y)) bad = true;
+          else lost[j] |= fpe_dot_step(res[j], err[j], p, x, y);
+        };
+        for (int row = r0 + threadIdx.x; row < r1; row += (kPair ? 2 : 1) * BLOCK) {
+          const int ahead = row + kPfSteps * BLOCK;
+          if ((threadIdx.x & 31) == 0 && ahead < r1) pf_fn(ctx, ahead);
+          if constexpr (kPair) {
+            if (row + BLOCK < r1) row2_fn(ctx, row, row + BLOCK, dep);
+            else row_fn(ctx, row, dep);
+          } else {
+            row_fn(ctx, row, dep);
+          }
+        }
+#pragma unroll
+        for (int j = 0; j < NACC; j++) {
+          lost[j] |= fpe_sum(res[j], err[j], p);
+          if (lost[j]) atomicOr(&R->flags, 2u << j);
+          Window win;
+          window_init(win);
+#pragma unroll 1
+          for (int i = 0; i < p; i++) {
+            double t = res[j][0];
+#pragma unroll
+            for (int k = 1; k < kFpeMax; k++)
+              if (i == k) t = res[j][k];
+            if (!is_zero_bits(t)) {
+              const ExactProd e = exact_product(t, 1.0);
+              bad |= e.bad;
+              exact_deposit(win, sacc + j * kNDig * kCopies, copy, e);
+            }
+          }
+          window_flush(win, sacc + j * kNDig * kCopies, copy);
+        }
+        if (bad) atomicOr(&R->flags, 1u);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < NACC; j++) smem_to_global(sacc + j * kNDig * kCopies, R->digits[j]);
       } else {
         // plain: one fixed-order partial per unit, summed in unit order at the end
         for (int k = k0; k < k1; k++) {
@@ -286,7 +356,7 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
       __syncthreads();
       if (us->last) {
         __threadfence();
-        if constexpr (V == RPCG_EXBLAS) {
+        if constexpr (V != RPCG_PLAIN) {
 #pragma unroll
           for (int j = 0; j < NACC; j++) {
             const double v = take_and_round(R->digits[j], us->dig, us->D, us->range);
@@ -295,6 +365,9 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
           }
           if (threadIdx.x == 0) {
             const unsigned int f = atomicExch(&R->flags, 0u);
+            // a non-finite operand makes every dot of the pass NaN (and, for
+            // fpe, inexact); otherwise bit j + 1 flags dot j's lost bits
+            us->lost = (f & 1u) ? (1u << NACC) - 1u : (f >> 1) & ((1u << NACC) - 1u);
             if (f & 1u)
               for (int j = 0; j < NACC; j++) us->value[j] = __longlong_as_double(0x7FF8000000000000ll);
           }
@@ -308,14 +381,76 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
           }
         }
         if (threadIdx.x == 0) {
+          if constexpr (V == RPCG_PLAIN) us->lost = 0u;
           R->counter = 0;
-          fin_fn(s, us->value);
+          fin_fn(s, us->value, V == RPCG_FPE ? us->lost : 0u);
         }
       }
       __syncthreads();
       a = run_end;
     }
   }
+}
+
+// ------------------------------------------------------------------ scalar steps (one thread)
+
+// S2: rho = beta / <d, w> (with the breakdown checks).
+static __device__ void b_finalize_a(SysState* t, double dw, BatchHead* head) {
+  if (!isfinite(dw)) {
+    t->status = RPCG_ERR_NONFINITE;
+    b_stop(t, head);
+    return;
+  }
+  if (!(dw > 0.0)) {
+    t->status = RPCG_ERR_NOT_SPD;
+    b_stop(t, head);
+    return;
+  }
+  t->beta_old = t->beta;
+  t->rho = __ddiv_rn(t->beta, dw);
+}
+
+// After S6 and S8: gamma, the iteration count, relres and the system's own
+// stopping test.
+static __device__ void b_finalize_b(const BatchDesc& B, int s, double beta, double tau) {
+  SysState* t = B.st + s;
+  const SysDev& S = B.sys[s];
+  t->beta = beta;
+  t->tau = tau;
+  if (!isfinite(beta) || !isfinite(tau)) {
+    t->status = RPCG_ERR_NONFINITE;
+    t->iter += 1;
+    b_stop(t, B.head);
+    return;
+  }
+  t->gamma = __ddiv_rn(beta, t->beta_old);
+  t->iter += 1;
+  t->rel = __ddiv_rn(__dsqrt_rn(tau), t->bnorm);
+  if (S.history) S.history[t->iter] = t->rel;
+  if (tau > 0.0 && !(beta > 0.0)) {
+    t->status = RPCG_ERR_NOT_SPD;
+    b_stop(t, B.head);
+    return;
+  }
+  if (!((t->rel >= S.tol) && (t->iter < S.max_iter))) {
+    t->active = 2;  // finished this iteration: pass C still updates d (unobservable), then it stops
+  }
+}
+
+// FPE variant, after a pass whose dots `lost` flags: count the inexact dots,
+// grow the adaptive size by one, and with fpe_strict = 0 mark the system
+// for the exact recomputation of the pass's dots (phase 1: pass A, 2: pass
+// B).  Returns true when the pass's finalisation waits for that.  The same
+// rules as the single-system passes.
+static __device__ bool b_fpe_inexact(const BatchDesc& B, int s, unsigned lost, int phase) {
+  if (!lost) return false;
+  SysState* t = B.st + s;
+  t->fpe_inexact += __popc(lost);
+  if (B.sys[s].fpe_size == 0 && t->fpe_p < kFpeMax) t->fpe_p += 1;
+  if (B.sys[s].fpe_strict) return false;
+  t->redo = phase;
+  atomicOr(&B.head->redo_any, phase);
+  return true;
 }
 
 // ------------------------------------------------------------------ kernels
@@ -350,6 +485,11 @@ static __global__ void k_b_init(BatchDesc B) {
     t.bzero = 0;
     t.active = B.sys[s].m.n > 0 ? 1 : 0;  // an empty system has no units: done at once
     t.pad = 0;
+    // the adaptive expansion size starts at 3, the size Sec. 4.3 finds enough for Poisson
+    t.fpe_p = B.sys[s].fpe_size > 0 ? B.sys[s].fpe_size : 3;
+    t.fpe_inexact = 0;
+    t.redo = 0;
+    t.pad2 = 0;
   }
   __shared__ int nact;
   if (threadIdx.x == 0) nact = 0;
@@ -360,7 +500,8 @@ static __global__ void k_b_init(BatchDesc B) {
   __syncthreads();
   if (threadIdx.x == 0) {
     B.head->active_count = nact;
-    for (int k = 0; k < 4; k++) B.head->work[k] = 0u;
+    B.head->redo_any = 0;
+    for (int k = 0; k < kWorkCounters; k++) B.head->work[k] = 0u;
   }
 }
 
@@ -378,6 +519,10 @@ static __global__ void k_b_init_list(BatchDesc B, const int* __restrict__ list, 
     t.active = B.sys[s].m.n > 0 ? 1 : 0;
     if (t.active) atomicAdd(&B.head->active_count, 1);
     t.pad = 0;
+    t.fpe_p = B.sys[s].fpe_size > 0 ? B.sys[s].fpe_size : 3;
+    t.fpe_inexact = 0;
+    t.redo = 0;
+    t.pad2 = 0;
   }
 }
 
@@ -426,7 +571,7 @@ __global__ void __launch_bounds__(BLOCK) k_b_setup(BatchDesc B, const int* __res
         dep(1, ri, ri);
         dep(2, bi, bi);
       },
-      [&](int s, const double* v) {
+      [&](int s, const double* v, unsigned) {
         SysState* t = B.st + s;
         const SysDev& S = B.sys[s];
         if (t->bad_row < S.m.n) {
@@ -465,7 +610,7 @@ __global__ void __launch_bounds__(BLOCK) k_b_setup(BatchDesc B, const int* __res
 }
 
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_b_pass_a(BatchDesc B) {
+__global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 512 / BLOCK : 768 / BLOCK) k_b_pass_a(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
   for_units<V, 1, BLOCK>(
       B, B.aprefix, &B.head->work[kWorkA], smem,
@@ -479,21 +624,10 @@ __global__ void __launch_bounds__(BLOCK, 768 / BLOCK) k_b_pass_a(BatchDesc B) {
         c.w[i] = v;
         dep(0, __ldg(c.d + i), v);
       },
-      [&](int s, const double* v) {
+      [&](int s, const double* v, unsigned lost) {
         SysState* t = B.st + s;
-        const double dw = v[0];
-        if (!isfinite(dw)) {
-          t->status = RPCG_ERR_NONFINITE;
-          b_stop(t, B.head);
-          return;
-        }
-        if (!(dw > 0.0)) {
-          t->status = RPCG_ERR_NOT_SPD;
-          b_stop(t, B.head);
-          return;
-        }
-        t->beta_old = t->beta;
-        t->rho = __ddiv_rn(t->beta, dw);
+        if (V == RPCG_FPE && b_fpe_inexact(B, s, lost, 1)) return;  // recomputed by k_b_redo_a
+        b_finalize_a(t, v[0], B.head);
       },
       [&](const PassACtx& c, int ia, int ib, auto dep) {
         double va, vb;
@@ -527,31 +661,10 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
         dep(0, zi, ri);
         dep(1, ri, ri);
       },
-      [&](int s, const double* v) {
-        SysState* t = B.st + s;
-        if (t->status != 0) return;
-        const SysDev& S = B.sys[s];
-        const double beta = v[0], tau = v[1];
-        t->beta = beta;
-        t->tau = tau;
-        if (!isfinite(beta) || !isfinite(tau)) {
-          t->status = RPCG_ERR_NONFINITE;
-          t->iter += 1;
-          b_stop(t, B.head);
-          return;
-        }
-        t->gamma = __ddiv_rn(beta, t->beta_old);
-        t->iter += 1;
-        t->rel = __ddiv_rn(__dsqrt_rn(tau), t->bnorm);
-        if (S.history) S.history[t->iter] = t->rel;
-        if (tau > 0.0 && !(beta > 0.0)) {
-          t->status = RPCG_ERR_NOT_SPD;
-          b_stop(t, B.head);
-          return;
-        }
-        if (!((t->rel >= S.tol) && (t->iter < S.max_iter))) {
-          t->active = 2;  // finished this iteration: pass C still updates d (unobservable), then it stops
-        }
+      [&](int s, const double* v, unsigned lost) {
+        if (B.st[s].status != 0) return;
+        if (V == RPCG_FPE && b_fpe_inexact(B, s, lost, 2)) return;  // recomputed by k_b_redo_b
+        b_finalize_b(B, s, v[0], v[1]);
       },
       [&](const PassBCtx& c, int ia, int ib, auto dep) {
         if (c.stopped) return;
@@ -569,6 +682,54 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
         dep(0, zb, rb);
         dep(1, rb, rb);
       });
+}
+
+// FPE variant with fpe_strict = 0: the systems whose pass A (or pass B) dots
+// were inexact recompute them exactly and take the pass's scalar step; the
+// other systems' units are skipped.  Nothing to do (and every CTA returns at
+// once) when no system asked.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_b_redo_a(BatchDesc B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (!(*(volatile int*)&B.head->redo_any & 1)) return;
+  for_units<RPCG_EXBLAS, 1, BLOCK>(
+      B, B.aprefix, &B.head->work[kWorkRA], smem,
+      [&](int s) {
+        const SysDev& S = B.sys[s];
+        return PassACtx{S.m, S.d, S.w};
+      },
+      [](const PassACtx&, int) {},
+      [&](const PassACtx& c, int i, auto dep) { dep(0, c.d[i], c.w[i]); },
+      [&](int s, const double* v, unsigned) {
+        SysState* t = B.st + s;
+        t->redo = 0;
+        b_finalize_a(t, v[0], B.head);
+      },
+      NullRow2{}, [&](int s) { return B.st[s].redo != 1; });
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK) k_b_redo_b(BatchDesc B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  if (!(*(volatile int*)&B.head->redo_any & 2)) return;
+  for_units<RPCG_EXBLAS, 2, BLOCK>(
+      B, B.aprefix, &B.head->work[kWorkRB], smem,
+      [&](int s) {
+        const SysDev& S = B.sys[s];
+        return PassBCtx{S.x, S.r, S.d, S.w, S.inv, 0.0, false};
+      },
+      [](const PassBCtx&, int) {},
+      [&](const PassBCtx& c, int i, auto dep) {
+        const double ri = c.r[i];
+        const double zi = __dmul_rn(c.inv[i], ri);
+        dep(0, zi, ri);
+        dep(1, ri, ri);
+      },
+      [&](int s, const double* v, unsigned) {
+        B.st[s].redo = 0;
+        b_finalize_b(B, s, v[0], v[1]);
+      },
+      NullRow2{}, [&](int s) { return B.st[s].redo != 2; });
 }
 
 // S7 for every listed system that is still running (no reduction: static split).
@@ -602,7 +763,8 @@ static __device__ void retire_and_list(BatchDesc B) {
   build_prefix(B, false);
   __syncthreads();
   if (threadIdx.x == 0) {
-    for (int k = 0; k < 4; k++) B.head->work[k] = 0u;
+    for (int k = 0; k < kWorkCounters; k++) B.head->work[k] = 0u;
+    B.head->redo_any = 0;
     __threadfence();
   }
 }
