@@ -54,19 +54,23 @@ def test_server_admits_work_while_others_run(rpcg, cuda):
     b_big = synth.rhs_uniform(big.n, 9)
     small = synth.poisson7(8)
     srv = rpcg.Server(hbm_budget_bytes=4 << 30, max_slots=8)
-    # tol below what any iterate reaches: the big solve runs its 3000
-    # iterations (hundreds of ms), so it is still running when the short
-    # requests arrive however fast the passes are
-    t_big = srv.submit(big, b_big, tol=1e-30, max_iter=3000)
-    time.sleep(0.02)
+    # tol 0: the big solve never meets the test (its residual shrinks by ~0.8
+    # per iteration, 1e-30 at iteration 286), so it runs until max_iter or
+    # until its residual underflows, thousands of iterations either way; the
+    # short requests are submitted once it has run two chunks of iterations
+    t_big = srv.submit(big, b_big, tol=0.0, max_iter=3000)
+    t0 = time.time()
+    while srv.stats()["chunks"] < 2 and time.time() - t0 < 60:
+        time.sleep(0.0005)
     t_small = [srv.submit(small, synth.rhs_uniform(small.n, 50 + k), tol=1e-8) for k in range(5)]
-    done_order = []
+    done_order, results = [], {}
     lock = threading.Lock()
 
     def waiter(t):
         x, r = srv.wait(t, timeout_us=120_000_000)
         with lock:
             done_order.append(t)
+            results[t] = r
 
     ths = [threading.Thread(target=waiter, args=(t,)) for t in [t_big] + t_small]
     for th in ths:
@@ -74,6 +78,8 @@ def test_server_admits_work_while_others_run(rpcg, cuda):
     for th in ths:
         th.join()
     srv.close()
+    assert results[t_big]["iterations"] > 1000, results[t_big]
+    assert all(results[t]["status"] == 0 for t in t_small)
     assert done_order[-1] == t_big, done_order
 
 
