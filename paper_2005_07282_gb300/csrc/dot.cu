@@ -153,11 +153,14 @@ __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __r
 // (Alg. 3); the threads' expansions then meet exactly in the long
 // accumulator and are rounded once, so the merge loses nothing and *exact
 // reports whether any thread's expansion lost bits (or a product fell below
-// twoprod's exact range).
+// twoprod's exact range).  The element steps of 3 warps in 8 run on the
+// integer pipes (fpe_dot_step_int, the same expansions), the others on the
+// FP64 pipe; capped at 64 registers, 32 warps per SM keep both busy
+// (2^26 pairs: 3.80 ms with every step in FP64 at 16 warps per SM, 2.61 ms).
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,
-                                                   const double* __restrict__ b, int p, DotScratch* ws, double* out,
-                                                   int32_t* exact) {
+__global__ void __launch_bounds__(BLOCK, 4) k_dot_fpe(int64_t n, const double* __restrict__ a,
+                                                      const double* __restrict__ b, int p, DotScratch* ws, double* out,
+                                                      int32_t* exact) {
   __shared__ unsigned long long sacc[kNDig * kCopies];
   __shared__ long long sdig[kNDig];
   __shared__ uint32_t sD[kNDig];
@@ -166,38 +169,16 @@ __global__ void __launch_bounds__(BLOCK) k_dot_fpe(int64_t n, const double* __re
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) res[i] = err[i] = 0.0;
   bool lost = false, nonfinite = false;
+  const bool int_warp = fpe_int_warp();
   const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * BLOCK;
-  // the expansion work of one element depends on the previous one, so the
-  // loads run one chunk of U elements ahead of it
-  constexpr int U = 4;
-  double xa[U], ya[U];
-#pragma unroll
-  for (int u = 0; u < U; u++) {
-    const int64_t i = tid + u * nthr;
-    xa[u] = i < n ? __ldcs(a + i) : 0.0;
-    ya[u] = i < n ? __ldcs(b + i) : 0.0;
-  }
-  for (int64_t i0 = tid; i0 < n; i0 += U * nthr) {
-    double xb[U], yb[U];
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      const int64_t i = i0 + (U + u) * nthr;
-      xb[u] = i < n ? __ldcs(a + i) : 0.0;
-      yb[u] = i < n ? __ldcs(b + i) : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      if (i0 + u * nthr < n) {
-        if (!is_finite_bits(xa[u]) || !is_finite_bits(ya[u])) nonfinite = true;
-        else lost |= fpe_dot_step(res, err, p, xa[u], ya[u]);
-      }
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) {
-      xa[u] = xb[u];
-      ya[u] = yb[u];
-    }
+  // compute-bound (the FP64 pipe, and the integer pipes in the warps that
+  // emulate it): no loads run ahead, which keeps registers for more warps
+  for (int64_t i = tid; i < n; i += nthr) {
+    const double x = __ldcs(a + i), y = __ldcs(b + i);
+    if (!is_finite_bits(x) || !is_finite_bits(y)) nonfinite = true;
+    else if (int_warp) lost |= fpe_dot_step_int(res, err, p, x, y, nonfinite);
+    else lost |= fpe_dot_step(res, err, p, x, y);
   }
   lost |= fpe_sum(res, err, p);
   Window win;
@@ -326,7 +307,7 @@ static rpcg_status dot_common(int kind, int64_t n, const double* a, const double
     if (kind == 0) {
       launch_dot_exact(n, a, b, ws, out, s);
     } else if (kind == 1) {
-      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
+      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kDotMaxGrid, 4), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
     } else {
       k_dot_plain<kDotBlock><<<dot_grid(n, 4, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
     }

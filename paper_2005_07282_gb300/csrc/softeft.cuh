@@ -24,6 +24,8 @@
 #pragma once
 #include <cstdint>
 
+#include "device.cuh"
+
 namespace rpcg {
 
 struct SF {
@@ -239,6 +241,35 @@ __device__ __forceinline__ bool sf_fpe_dot_step(double (&res)[PMAX], double (&er
   lost |= sf_accumulate(res, p, r, bad).m != 0;
   if (s.m != 0) lost |= sf_accumulate(err, p, s, bad).m != 0;
   return lost | bad;
+}
+
+// One element of the FPE dot on the integer pipe with the expansions and
+// flag of fpe_dot_step: twoprod and Alg. 4's twosums as exact integer
+// arithmetic.  A product whose error is not representable (|r| < 2^-969)
+// or that overflows takes fpe_dot_step itself (both flag it as inexact).
+// A sum that overflows sets `nonfinite` (fpe_dot_step leaves an infinite
+// term there, which makes the dot NaN when the terms are deposited), so the
+// results agree in that case too.  a, b finite.
+__device__ __forceinline__ bool fpe_dot_step_int(double (&res)[kFpeMax], double (&err)[kFpeMax], int p, double a,
+                                                 double b, bool& nonfinite) {
+  if (is_zero_bits(a) || is_zero_bits(b)) return false;  // adds nothing
+  bool bad = false;
+  SF r, s;
+  sf_twoprod(a, b, r, s, bad);
+  if (bad || sf_below_twoprod_safe(r)) return fpe_dot_step(res, err, p, a, b);
+  bool lost = sf_accumulate(res, p, r, bad).m != 0;
+  if (s.m != 0) lost |= sf_accumulate(err, p, s, bad).m != 0;
+  nonfinite |= bad;
+  return lost | bad;
+}
+
+// GB300's FP64 pipe is its scarce unit: 3 of every 8 warps of a CTA run the
+// FPE dot's element steps on the integer pipes instead (fpe_dot_step_int
+// gives the same expansions), so both kinds of pipe work at once.
+// Warp-uniform.
+__device__ __forceinline__ bool fpe_int_warp() {
+  const int nw = (int)(blockDim.x >> 5);
+  return (int)(threadIdx.x >> 5) < (3 * nw + 4) / 8;
 }
 
 }  // namespace rpcg

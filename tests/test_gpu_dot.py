@@ -131,6 +131,46 @@ def test_dot_fpe_flag_cases(rpcg, cuda):
     assert ex.item() == 1 and same(v.item(), 0.0)
 
 
+def _one_thread(vals_a, vals_b, t, n=2048, nthr=256):
+    """Arrays of n pairs whose non-zero products all land in thread t of the
+    FPE dot's single CTA (thread t takes elements t, t + 256, ...)."""
+    a, b = np.zeros(n), np.zeros(n)
+    for k, (x, y) in enumerate(zip(vals_a, vals_b)):
+        a[t + k * nthr], b[t + k * nthr] = x, y
+    return a, b
+
+
+@pytest.mark.parametrize("p", [1, 2, 8])
+def test_dot_fpe_integer_and_fp64_warps_agree(rpcg, cuda, oracle_lib, p):
+    """A share of the FPE dot's warps runs the element steps on the integer
+    pipes, the rest in FP64.  A thread's expansion depends only on its own
+    products, so the same products placed in a thread of either kind of warp
+    give the same value and flag, bit for bit: lossy ill-conditioned sums,
+    products below twoprod's exact range, subnormal products, sums that
+    overflow, cancellation to zero."""
+    rng = np.random.default_rng(5)
+    c40a, c40b = synth.dot_family_c(8, 1e40, 3)
+    cases = [
+        (c40a, c40b),
+        (rng.uniform(-1, 1, 8), rng.uniform(-1, 1, 8)),
+        ([2.0 ** -600, 1.0, -3.0, 2.0 ** -500, 5.0, 7.0, 1e-300, 9.0], [2.0 ** -500, 1.0, 3.0, 2.0 ** -560, 1.5, 1.0, 1e-20, 2.0]),
+        ([1.5 * 2.0 ** 1000] * 8, [1.9 * 2.0 ** 23] * 8),                  # the running sum overflows
+        ([1.0, -1.0, 2.0 ** 60, -(2.0 ** 60), 3.0, -3.0, 0.5, -0.5], [1.0] * 8),  # cancels to +0
+        ([2.0 ** -1074, 3.0, 2.0 ** -1000, 1.0, 1.0, 1.0, 1.0, 1.0], [1.0, 2.0 ** -1074, 2.0 ** -30, 1e-16, 1.0, -1e-16, 3.0, 2.0 ** 52]),
+    ]
+    # threads 0, 40 and 95 are in warps 0-2 (integer pipes); 96, 160 and 255 in FP64 warps
+    for va, vb in cases:
+        got = []
+        for t in (0, 40, 95, 96, 160, 255):
+            a, b = _one_thread(va, vb, t)
+            v, ex = rpcg.dot_fpe(_dev(a, cuda), _dev(b, cuda), p=p)
+            got.append((bits([v.item()])[0] if not math.isnan(v.item()) else "nan", ex.item()))
+        assert len(set(got)) == 1, (va, got)
+        if got[0][1] == 1:
+            a, b = _one_thread(va, vb, 0)
+            assert same(v.item(), oracle_lib.dot_exact(a, b))
+
+
 def test_dot_plain_close(rpcg, cuda, oracle_lib):
     a, b = synth.dot_family_a(1000003, 12)
     want = oracle_lib.dot_exact(a, b, nthreads=4)
