@@ -26,6 +26,7 @@
 
 #include "device.cuh"
 #include "host.h"
+#include "softeft.cuh"
 #include "solver.cuh"
 
 namespace rpcg {
@@ -104,6 +105,7 @@ __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long*
     exact_deposit(R.win[j], sacc + j * kNDig * kCopies, threadIdx.x & (kCopies - 1), e);
   } else if constexpr (V == RPCG_FPE) {
     if (!is_finite_bits(a) || !is_finite_bits(b)) R.bad = true;
+    else if (fpe_int_warp()) R.lost[j] |= fpe_dot_step_int(R.res[j], R.err[j], p, a, b, R.bad);
     else R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b);
   } else {
     R.acc[j] = __fma_rn(a, b, R.acc[j]);
@@ -315,7 +317,7 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(MatDev m, const double* __restri
 
 // Pass A: S1 + S2.
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
+__global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 1) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
                                                   PassScratch* ws, SolveState* st, const SolveArgs* args,
                                                   cudaGraphConditionalHandle cond) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -423,6 +425,78 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
       }
     }
     finalize_b(fs->value[0], fs->value[1], st, args, cond);
+  }
+}
+
+// FPE variant: pass B as two kernels, so that each thread holds one pair of
+// expansions instead of two.  With that, 64 registers (32 warps per SM)
+// suffice and a share of the warps can run their element steps on the
+// integer pipes (fpe_int_warp), while the rest use the FP64 pipe.  B1: S3,
+// S4, S5 and S6 (<z,r>, kept in the state); B2: S8 (<r,r> of the new r)
+// and the finalisation of both dots, with the counting and recompute rules
+// of pass B.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_b1(int n, const double* __restrict__ d,
+                                                                 const double* __restrict__ w,
+                                                                 const double* __restrict__ inv, double* __restrict__ r,
+                                                                 PassScratch* ws, SolveState* st, const SolveArgs* args,
+                                                                 cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<RPCG_FPE, 1>(smem, sacc);
+  if (st->status != 0 || st->redo) {
+    if (st->status != 0 && blockIdx.x == 0 && threadIdx.x == 0) stop_loop(st, args, cond);
+    return;
+  }
+  const int p = st->fpe_p;
+  double* __restrict__ x = args->x;
+  const double rho = st->rho, nrho = -st->rho;
+  smem_acc_zero(sacc);
+  __syncthreads();
+  Reducer<RPCG_FPE, 1> R;
+  red_init(R);
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const double xi = __fma_rn(rho, __ldcs(d + i), __ldcs(x + i));
+    const double ri = __fma_rn(nrho, __ldcs(w + i), __ldcs(r + i));
+    const double zi = __dmul_rn(__ldcs(inv + i), ri);
+    __stcs(x + i, xi);
+    r[i] = ri;  // read again by B2
+    red_add(R, sacc, 0, zi, ri, p);
+  }
+  if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
+    st->zr = fs->value[0];
+    st->zr_lost = fs->lost[0];
+  }
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_b2(int n, const double* __restrict__ r, PassScratch* ws,
+                                                                 SolveState* st, const SolveArgs* args,
+                                                                 cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<RPCG_FPE, 1>(smem, sacc);
+  if (st->status != 0 || st->redo) return;  // B1 has stopped the loop
+  const int p = st->fpe_p;
+  smem_acc_zero(sacc);
+  __syncthreads();
+  Reducer<RPCG_FPE, 1> R;
+  red_init(R);
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
+    const double ri = __ldcs(r + i);
+    red_add(R, sacc, 0, ri, ri, p);
+  }
+  if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
+    const bool lost0 = st->zr_lost != 0, lost1 = fs->lost[0] != 0;
+    if (lost0 || lost1) {
+      st->fpe_inexact += (lost0 ? 1 : 0) + (lost1 ? 1 : 0);
+      fpe_grow(st, args);
+      if (!args->fpe_strict) {
+        st->redo = 2;  // recompute both dots exactly (k_redo_b)
+        return;
+      }
+    }
+    finalize_b(st->zr, fs->value[0], st, args, cond);
   }
 }
 
@@ -632,6 +706,10 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
   RPCG_CUDA_TRY(set_smem(k_spmv<BLOCK>, c->smem_spmv));
   RPCG_CUDA_TRY(set_smem(k_pass_a<V, BLOCK>, c->smem_a));
   RPCG_CUDA_TRY(set_smem(k_pass_b<V, BLOCK>, c->smem_b));
+  if (V == RPCG_FPE) {
+    RPCG_CUDA_TRY(set_smem(k_pass_b1<BLOCK>, c->smem_a));  // one FPE dot each, as pass A
+    RPCG_CUDA_TRY(set_smem(k_pass_b2<BLOCK>, c->smem_a));
+  }
   RPCG_CUDA_TRY(set_smem(k_setup<V, BLOCK>, c->smem_s));
   RPCG_CUDA_TRY(set_smem(k_redo_a<BLOCK>, c->smem_ra));
   RPCG_CUDA_TRY(set_smem(k_redo_b<BLOCK>, c->smem_rb));
@@ -698,7 +776,14 @@ static rpcg_status build_graph(rpcg_matrix_t A, int grid, cudaGraph_t* out_graph
     RPCG_CUDA_TRY(add_kernel(body, &b_ra, &prev, 1, (const void*)k_redo_a<BLOCK>, grid_stream, BLOCK, smem_ra, a));
     prev = b_ra;
   }
-  {
+  if (V == RPCG_FPE) {
+    void* a1[] = {&n, &d, &w, &inv, &r, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_b, &prev, 1, (const void*)k_pass_b1<BLOCK>, grid_stream, BLOCK, smem_a, a1));
+    prev = b_b;
+    void* a2[] = {&n, &r, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_b, &prev, 1, (const void*)k_pass_b2<BLOCK>, grid_stream, BLOCK, smem_a, a2));
+    prev = b_b;
+  } else {
     void* a[] = {&n, &d, &w, &inv, &r, &ws, &st, &args, &cond};
     RPCG_CUDA_TRY(add_kernel(body, &b_b, &prev, 1, (const void*)k_pass_b<V, BLOCK>, grid_stream, BLOCK, smem_b, a));
     prev = b_b;
@@ -797,7 +882,12 @@ static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaSt
     cudaEventRecord(ev[3], s);
     if (V == RPCG_FPE) k_redo_a<BLOCK><<<c.grid_stream, BLOCK, c.smem_ra, s>>>(n, d, w, ws, st, args, cond);
     cudaEventRecord(ev[4], s);
-    k_pass_b<V, BLOCK><<<c.grid_stream, BLOCK, c.smem_b, s>>>(n, d, w, inv, r, ws, st, args, cond);
+    if (V == RPCG_FPE) {
+      k_pass_b1<BLOCK><<<c.grid_stream, BLOCK, c.smem_a, s>>>(n, d, w, inv, r, ws, st, args, cond);
+      k_pass_b2<BLOCK><<<c.grid_stream, BLOCK, c.smem_a, s>>>(n, r, ws, st, args, cond);
+    } else {
+      k_pass_b<V, BLOCK><<<c.grid_stream, BLOCK, c.smem_b, s>>>(n, d, w, inv, r, ws, st, args, cond);
+    }
     cudaEventRecord(ev[5], s);
     if (V == RPCG_FPE) k_redo_b<BLOCK><<<c.grid_stream, BLOCK, c.smem_rb, s>>>(n, inv, r, ws, st, args, cond);
     cudaEventRecord(ev[6], s);

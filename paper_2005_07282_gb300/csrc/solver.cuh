@@ -32,6 +32,9 @@ struct SolveArgs {
 struct SolveState {
   double rho, beta, beta_old, tau, gamma, bnorm, rel;
   int iter, status, bad_row, bzero, redo, fpe_inexact, active, fpe_p;  // fpe_p: expansion size in use
+  double zr;    // fpe variant, multi-pass path: <z,r> of pass B1, finished with <r,r> in pass B2
+  int zr_lost;  // and whether its expansions lost bits (or met a non-finite operand)
+  int pad;
 };
 
 // Device matrix.  The handle stores A in SELL-32 form: rows are grouped
