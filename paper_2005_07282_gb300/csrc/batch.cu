@@ -132,6 +132,10 @@ static rpcg_status batch_plan(rpcg_batch_t B, const rpcg_batch_s::Layout* L, Bat
   P->g_q = occ_grid((const void*)k_b_inv_q, 0);
   P->g_ra = P->g_rb = 1;
   if constexpr (V == RPCG_FPE) {
+    // pass B runs as B1 + B2 (one FPE dot each, the shared memory of pass A)
+    RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b1<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm1));
+    RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b2<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm1));
+    P->g_b = occ_grid((const void*)k_b_pass_b1<BLOCK>, P->sm1);
     RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_redo_a<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smr1));
     RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_redo_b<BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->smr2));
     P->g_ra = occ_grid((const void*)k_b_redo_a<BLOCK>, P->smr1);
@@ -189,7 +193,13 @@ static rpcg_status batch_graph(rpcg_batch_t B, int tile, cudaGraph_t* out_g, cud
       RPCG_CUDA_TRY(add_node(body, &b_ra, &b_a, 1, (const void*)k_b_redo_a<BLOCK>, P.g_ra, BLOCK, P.smr1, a));
       b_a = b_ra;
     }
-    RPCG_CUDA_TRY(add_node(body, &b_b, &b_a, 1, (const void*)k_b_pass_b<V, BLOCK>, g_b, BLOCK, sm2, a));
+    if constexpr (V == RPCG_FPE) {
+      cudaGraphNode_t b_b1;
+      RPCG_CUDA_TRY(add_node(body, &b_b1, &b_a, 1, (const void*)k_b_pass_b1<BLOCK>, P.g_b, BLOCK, sm1, a));
+      RPCG_CUDA_TRY(add_node(body, &b_b, &b_b1, 1, (const void*)k_b_pass_b2<BLOCK>, P.g_b, BLOCK, sm1, a));
+    } else {
+      RPCG_CUDA_TRY(add_node(body, &b_b, &b_a, 1, (const void*)k_b_pass_b<V, BLOCK>, g_b, BLOCK, sm2, a));
+    }
     if constexpr (V == RPCG_FPE) {
       cudaGraphNode_t b_rb;
       RPCG_CUDA_TRY(add_node(body, &b_rb, &b_b, 1, (const void*)k_b_redo_b<BLOCK>, P.g_rb, BLOCK, P.smr2, a));
@@ -363,8 +373,13 @@ static rpcg_status batch_eager(rpcg_batch_t B, int tile, cudaStream_t s, float* 
       if (V == RPCG_FPE) k_b_redo_a<BLOCK><<<P.g_ra, BLOCK, P.smr1, s>>>(D);
     });
     timed(2, 1, [&] {
-      k_b_pass_b<V, BLOCK><<<P.g_b, BLOCK, P.sm2, s>>>(D);
-      if (V == RPCG_FPE) k_b_redo_b<BLOCK><<<P.g_rb, BLOCK, P.smr2, s>>>(D);
+      if (V == RPCG_FPE) {
+        k_b_pass_b1<BLOCK><<<P.g_b, BLOCK, P.sm1, s>>>(D);
+        k_b_pass_b2<BLOCK><<<P.g_b, BLOCK, P.sm1, s>>>(D);
+        k_b_redo_b<BLOCK><<<P.g_rb, BLOCK, P.smr2, s>>>(D);
+      } else {
+        k_b_pass_b<V, BLOCK><<<P.g_b, BLOCK, P.sm2, s>>>(D);
+      }
     });
     timed(3, 1, [&] { k_b_pass_c<BLOCK><<<P.g_c, BLOCK, 0, s>>>(D); });
     timed(4, 1, [&] { k_b_retire<<<1, 256, 0, s>>>(D); });

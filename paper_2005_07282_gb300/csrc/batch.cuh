@@ -19,6 +19,7 @@
 #include <type_traits>
 
 #include "device.cuh"
+#include "softeft.cuh"
 #include "solver.cuh"
 
 namespace rpcg {
@@ -41,6 +42,8 @@ struct SysState {
   int iter, status, bad_row, bzero, active, pad;
   int fpe_p, fpe_inexact;  // fpe variant: expansion size in use, inexact dots seen
   int redo, pad2;          // fpe variant: 1 / 2 = pass A's / pass B's dots to recompute exactly
+  double zr;               // fpe variant: <z,r> of pass B1, finished with <r,r> in pass B2
+  int zr_lost, pad3;
 };
 
 // per-system reduction scratch (digits, arrival counter, flags)
@@ -51,7 +54,7 @@ struct SysRed {
 };
 
 constexpr int kChunkUnits = 4;  // listed units a CTA takes at a time
-enum { kWorkSetup = 0, kWorkA = 1, kWorkB = 2, kWorkRA = 3, kWorkRB = 4, kWorkCounters = 6 };
+enum { kWorkSetup = 0, kWorkA = 1, kWorkB = 2, kWorkRA = 3, kWorkRB = 4, kWorkB2 = 5, kWorkCounters = 6 };
 
 struct BatchHead {
   int active_count;  // systems still iterating
@@ -194,13 +197,16 @@ __host__ __device__ constexpr size_t b_smem(int nacc, int count) {
 // row2_fn(ctx, ra, rb, dep) does rows ra and rb together (both in range);
 // pass a NullRow2 to process rows one at a time.  skip_fn(sys) == true
 // skips a system's units altogether (no deposit, no arrival, no fin_fn).
+// kIntShare (fpe): a share of the warps run the element steps on the
+// integer pipes (fpe_int_warp); it pays in kernels light enough for 32
+// warps per SM (measured: the split FPE pass B), not in pass A.
 struct NullRow2 {};
 struct NoSkip {
   __device__ bool operator()(int) const { return false; }
 };
 
-template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn, class Row2Fn = NullRow2,
-          class SkipFn = NoSkip>
+template <int V, int NACC, int BLOCK, bool kIntShare = false, class CtxFn, class PfFn, class RowFn, class FinFn,
+          class Row2Fn = NullRow2, class SkipFn = NoSkip>
 __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restrict__ prefix, unsigned int* work,
                                           unsigned char* smem, CtxFn ctx_fn, PfFn pf_fn, RowFn row_fn,
                                           FinFn fin_fn, Row2Fn row2_fn = NullRow2{}, SkipFn skip_fn = NoSkip{}) {
@@ -287,8 +293,10 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         smem_acc_zero(sacc, NACC);
         __syncthreads();
         const int r0 = k0 * B.tile, r1 = min(n, k1 * B.tile);
+        const bool int_warp = kIntShare && fpe_int_warp();
         auto dep = [&](int j, double x, double y) {
           if (!is_finite_bits(x) || !is_finite_bits(y)) bad = true;
+          else if (int_warp) lost[j] |= fpe_dot_step_int(res[j], err[j], p, x, y, bad);
           else lost[j] |= fpe_dot_step(res[j], err[j], p, x, y);
         };
         for (int row = r0 + threadIdx.x; row < r1; row += (kPair ? 2 : 1) * BLOCK) {
@@ -681,6 +689,61 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
         dep(1, ra, ra);
         dep(0, zb, rb);
         dep(1, rb, rb);
+      });
+}
+
+// FPE variant: pass B as two passes, so that each thread holds one pair of
+// expansions (64 registers, a share of the warps on the integer pipes), as
+// in the single-system solve.  B1: S3-S6 (<z,r>, kept in the system's
+// state); B2: S8 (<r,r> of the new r) and the finalisation of both dots.
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_b1(BatchDesc B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for_units<RPCG_FPE, 1, BLOCK, true>(
+      B, B.aprefix, &B.head->work[kWorkB], smem,
+      [&](int s) {
+        const SysDev& S = B.sys[s];
+        const SysState& t = B.st[s];
+        return PassBCtx{S.x, S.r, S.d, S.w, S.inv, t.rho, t.status != 0};
+      },
+      [](const PassBCtx&, int) {},
+      [&](const PassBCtx& c, int i, auto dep) {
+        if (c.stopped) return;  // stopped in pass A of this iteration
+        const double xi = __fma_rn(c.rho, c.d[i], c.x[i]);
+        const double ri = __fma_rn(-c.rho, c.w[i], c.r[i]);
+        const double zi = __dmul_rn(c.inv[i], ri);
+        c.x[i] = xi;
+        c.r[i] = ri;
+        dep(0, zi, ri);
+      },
+      [&](int s, const double* v, unsigned lost) {
+        SysState* t = B.st + s;
+        t->zr = v[0];
+        t->zr_lost = (int)(lost & 1u);
+      });
+}
+
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_b2(BatchDesc B) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  for_units<RPCG_FPE, 1, BLOCK, true>(
+      B, B.aprefix, &B.head->work[kWorkB2], smem,
+      [&](int s) {
+        const SysDev& S = B.sys[s];
+        return PassBCtx{S.x, S.r, S.d, S.w, S.inv, 0.0, B.st[s].status != 0};
+      },
+      [](const PassBCtx&, int) {},
+      [&](const PassBCtx& c, int i, auto dep) {
+        if (c.stopped) return;
+        const double ri = c.r[i];
+        dep(0, ri, ri);
+      },
+      [&](int s, const double* v, unsigned lost) {
+        SysState* t = B.st + s;
+        if (t->status != 0) return;
+        const unsigned both = (t->zr_lost ? 1u : 0u) | ((lost & 1u) << 1);
+        if (b_fpe_inexact(B, s, both, 2)) return;  // recomputed by k_b_redo_b
+        b_finalize_b(B, s, t->zr, v[0]);
       });
 }
 

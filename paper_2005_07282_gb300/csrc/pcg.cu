@@ -96,7 +96,10 @@ __device__ __forceinline__ FinalScratch* red_carve(unsigned char* base, unsigned
   return fs;
 }
 
-template <int V, int NACC>
+// kIntShare (fpe): a share of the warps run the element steps on the
+// integer pipes (fpe_int_warp): in kernels capped at 64 registers for 32
+// warps per SM, where both kinds of pipe then stay busy.
+template <int V, int NACC, bool kIntShare = false>
 __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long* sacc, int j, double a, double b,
                                         int p) {
   if constexpr (V == RPCG_EXBLAS) {
@@ -105,7 +108,7 @@ __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long*
     exact_deposit(R.win[j], sacc + j * kNDig * kCopies, threadIdx.x & (kCopies - 1), e);
   } else if constexpr (V == RPCG_FPE) {
     if (!is_finite_bits(a) || !is_finite_bits(b)) R.bad = true;
-    else if (fpe_int_warp()) R.lost[j] |= fpe_dot_step_int(R.res[j], R.err[j], p, a, b, R.bad);
+    else if (kIntShare && fpe_int_warp()) R.lost[j] |= fpe_dot_step_int(R.res[j], R.err[j], p, a, b, R.bad);
     else R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b);
   } else {
     R.acc[j] = __fma_rn(a, b, R.acc[j]);
@@ -315,7 +318,10 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(MatDev m, const double* __restri
   for (int row = blockIdx.x * BLOCK + threadIdx.x; row < m.n; row += gridDim.x * BLOCK) y[row] = sell_row(m, row, x);
 }
 
-// Pass A: S1 + S2.
+// Pass A: S1 + S2.  The fpe variant's pass A (SpMV and one FPE dot) is
+// capped at 64 registers with a share of its warps on the integer pipes:
+// 291 iterations/s on the 27-point 256^3 system, 259 without the cap.
+constexpr bool kPassAIntShare = true;
 template <int V, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 1) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
                                                   PassScratch* ws, SolveState* st, const SolveArgs* args,
@@ -335,7 +341,7 @@ __global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 1) k_pas
   for (int row = blockIdx.x * BLOCK + threadIdx.x; row < m.n; row += gridDim.x * BLOCK) {
     const double v = sell_row(m, row, d);
     w[row] = v;
-    red_add(R, sacc, 0, __ldg(d + row), v, p);
+    red_add<V, 1, kPassAIntShare>(R, sacc, 0, __ldg(d + row), v, p);
   }
   if (red_finish<V, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     if (st->status != 0) {
@@ -461,7 +467,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_b1(int n, const do
     const double zi = __dmul_rn(__ldcs(inv + i), ri);
     __stcs(x + i, xi);
     r[i] = ri;  // read again by B2
-    red_add(R, sacc, 0, zi, ri, p);
+    red_add<RPCG_FPE, 1, true>(R, sacc, 0, zi, ri, p);
   }
   if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     st->zr = fs->value[0];
@@ -484,7 +490,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_b2(int n, const do
   red_init(R);
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
     const double ri = __ldcs(r + i);
-    red_add(R, sacc, 0, ri, ri, p);
+    red_add<RPCG_FPE, 1, true>(R, sacc, 0, ri, ri, p);
   }
   if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     const bool lost0 = st->zr_lost != 0, lost1 = fs->lost[0] != 0;
