@@ -320,10 +320,13 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(MatDev m, const double* __restri
 
 // Pass A: S1 + S2.  The fpe variant's pass A (SpMV and one FPE dot) is
 // capped at 64 registers with a share of its warps on the integer pipes:
-// 291 iterations/s on the 27-point 256^3 system, 259 without the cap.
+// 291 iterations/s on the 27-point 256^3 system, 259 without the cap.  The
+// other variants keep the compiler's own register choice (minimum blocks 0:
+// an explicit 1 let the exact pass A grow to 110 registers and fall from
+// 1.01 to 1.51 ms at 256^3).
 constexpr bool kPassAIntShare = true;
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 1) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
+__global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 0) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
                                                   PassScratch* ws, SolveState* st, const SolveArgs* args,
                                                   cudaGraphConditionalHandle cond) {
   extern __shared__ __align__(16) unsigned char smem[];
