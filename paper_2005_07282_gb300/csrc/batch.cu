@@ -117,7 +117,8 @@ static rpcg_status batch_plan(rpcg_batch_t B, const rpcg_batch_s::Layout* L, Bat
   P->smr2 = b_smem<RPCG_EXBLAS>(2, count);
   RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_setup<VS, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm3));
   RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_a<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm1));
-  RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm2));
+  if constexpr (V != RPCG_FPE)  // the fpe variant's pass B is k_b_pass_b1 + k_b_pass_b2 (below)
+    RPCG_CUDA_TRY(cudaFuncSetAttribute((const void*)k_b_pass_b<V, BLOCK>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)P->sm2));
   auto occ_grid = [&](const void* f, size_t smem) {
     int occ = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, f, BLOCK, smem) != cudaSuccess || occ < 1) occ = 1;
@@ -127,7 +128,7 @@ static rpcg_status batch_plan(rpcg_batch_t B, const rpcg_batch_s::Layout* L, Bat
   };
   P->g_setup = occ_grid((const void*)k_b_setup<VS, BLOCK>, P->sm3);
   P->g_a = occ_grid((const void*)k_b_pass_a<V, BLOCK>, P->sm1);
-  P->g_b = occ_grid((const void*)k_b_pass_b<V, BLOCK>, P->sm2);
+  if constexpr (V != RPCG_FPE) P->g_b = occ_grid((const void*)k_b_pass_b<V, BLOCK>, P->sm2);
   P->g_c = occ_grid((const void*)k_b_pass_c<BLOCK>, 0);
   P->g_q = occ_grid((const void*)k_b_inv_q, 0);
   P->g_ra = P->g_rb = 1;
@@ -373,7 +374,7 @@ static rpcg_status batch_eager(rpcg_batch_t B, int tile, cudaStream_t s, float* 
       if (V == RPCG_FPE) k_b_redo_a<BLOCK><<<P.g_ra, BLOCK, P.smr1, s>>>(D);
     });
     timed(2, 1, [&] {
-      if (V == RPCG_FPE) {
+      if constexpr (V == RPCG_FPE) {
         k_b_pass_b1<BLOCK><<<P.g_b, BLOCK, P.sm1, s>>>(D);
         k_b_pass_b2<BLOCK><<<P.g_b, BLOCK, P.sm1, s>>>(D);
         k_b_redo_b<BLOCK><<<P.g_rb, BLOCK, P.smr2, s>>>(D);

@@ -714,10 +714,11 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
   c->smem_rb = pass_smem<RPCG_EXBLAS, 2>();
   RPCG_CUDA_TRY(set_smem(k_spmv<BLOCK>, c->smem_spmv));
   RPCG_CUDA_TRY(set_smem(k_pass_a<V, BLOCK>, c->smem_a));
-  RPCG_CUDA_TRY(set_smem(k_pass_b<V, BLOCK>, c->smem_b));
-  if (V == RPCG_FPE) {
+  if constexpr (V == RPCG_FPE) {
     RPCG_CUDA_TRY(set_smem(k_pass_b1<BLOCK>, c->smem_a));  // one FPE dot each, as pass A
     RPCG_CUDA_TRY(set_smem(k_pass_b2<BLOCK>, c->smem_a));
+  } else {
+    RPCG_CUDA_TRY(set_smem(k_pass_b<V, BLOCK>, c->smem_b));
   }
   RPCG_CUDA_TRY(set_smem(k_setup<V, BLOCK>, c->smem_s));
   RPCG_CUDA_TRY(set_smem(k_redo_a<BLOCK>, c->smem_ra));
@@ -785,7 +786,7 @@ static rpcg_status build_graph(rpcg_matrix_t A, int grid, cudaGraph_t* out_graph
     RPCG_CUDA_TRY(add_kernel(body, &b_ra, &prev, 1, (const void*)k_redo_a<BLOCK>, grid_stream, BLOCK, smem_ra, a));
     prev = b_ra;
   }
-  if (V == RPCG_FPE) {
+  if constexpr (V == RPCG_FPE) {
     void* a1[] = {&n, &d, &w, &inv, &r, &ws, &st, &args, &cond};
     RPCG_CUDA_TRY(add_kernel(body, &b_b, &prev, 1, (const void*)k_pass_b1<BLOCK>, grid_stream, BLOCK, smem_a, a1));
     prev = b_b;
@@ -891,7 +892,7 @@ static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaSt
     cudaEventRecord(ev[3], s);
     if (V == RPCG_FPE) k_redo_a<BLOCK><<<c.grid_stream, BLOCK, c.smem_ra, s>>>(n, d, w, ws, st, args, cond);
     cudaEventRecord(ev[4], s);
-    if (V == RPCG_FPE) {
+    if constexpr (V == RPCG_FPE) {
       k_pass_b1<BLOCK><<<c.grid_stream, BLOCK, c.smem_a, s>>>(n, d, w, inv, r, ws, st, args, cond);
       k_pass_b2<BLOCK><<<c.grid_stream, BLOCK, c.smem_a, s>>>(n, r, ws, st, args, cond);
     } else {
