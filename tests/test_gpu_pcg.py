@@ -116,6 +116,31 @@ def test_pcg_exblas_equals_fpe_small_p(rpcg, cuda, oracle_lib):
     assert len(set(res)) == 1
 
 
+@pytest.mark.parametrize("fpe_size", [1, 2, 0, 8])
+@pytest.mark.parametrize("kw", [{}, {"block": 128, "grid": 37}])
+def test_pcg_fpe_multipass_exact_trajectory(rpcg, cuda, oracle_lib, fpe_size, kw):
+    """The multi-pass fpe solve (pass B as B1 + B2, part of the warps on the
+    integer emulation) on systems too large for the cluster path: for every
+    expansion size (1 and 2 lose bits in most dots and take the exact
+    recomputation) the iterates, history and iteration count are the
+    oracle's exact-dot ones, bit for bit."""
+    import torch
+    for A in (synth.poisson27(30), synth.diffusion7(27, SEED + 12)[0]):  # 27000 and 19683 rows
+        M = rpcg.Matrix.from_csr(A)
+        assert M.solve_path("fpe", **kw) == "graph"
+        b = _rhs(oracle_lib, A, SEED + 13)
+        ref = oracle_lib.pcg(A, b, variant=oracle_lib.EXACT, tol=1e-9, max_iter=3000, nthreads=4)
+        x = torch.zeros(A.n, dtype=torch.float64, device=cuda)
+        hist = torch.full((3001,), float("nan"), dtype=torch.float64, device=cuda)
+        r = M.solve(_dev(b, cuda), x, variant="fpe", tol=1e-9, max_iter=3000, fpe_size=fpe_size, history=hist, **kw)
+        assert r["status"] == ref["status"] == 0
+        assert r["iterations"] == ref["iterations"]
+        assert np.array_equal(bits(x.cpu().numpy()), bits(ref["x"]))
+        assert np.array_equal(bits(hist[: r["iterations"] + 1].cpu().numpy()), bits(ref["history"]))
+        if fpe_size == 1:
+            assert r["fpe_inexact_count"] > 0
+
+
 def test_pcg_plain_converges(rpcg, cuda, oracle_lib):
     import torch
     A = synth.poisson7(16)
