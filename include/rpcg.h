@@ -100,7 +100,8 @@ const char *rpcg_last_error(void);
  * with n rows and nnz nonzeros; the handle also computes the Jacobi
  * preconditioner's inverse diagonal on first use).
  *   A_out     receives the handle.
- *   n, nnz    rows and nonzeros, 0 <= n < 2^31, 0 <= nnz < 2^31.
+ *   n, nnz    rows and nonzeros, 0 <= n <= 2^31 - 2^25 (headroom for 32-bit
+ *             row indices), 0 <= nnz < 2^31.
  *   rowptr, col, val   CSR arrays (n + 1, nnz, nnz entries).
  *   ptr_kind  0 = the three arrays are host pointers, 1 = device pointers.
  * The handle copies the arrays into device memory it owns (padded for
@@ -291,7 +292,7 @@ rpcg_status rpcg_solve_host(rpcg_matrix_t A, const double *b_host, double *x_hos
  *             RPCG_FPE_INEXACT), or RPCG_PLAIN.
  *   o         options; o->history, if set, is a device array of
  *             count x (max_iter + 1) doubles (row i for system i).
- *             o->block (0, 128, 256) and o->tile (0 or rows per unit): a zero
+ *             o->block (0, 128, 256) and o->tile (0, or 1..2^24 rows per unit): a zero
  *             picks them with the autotuner on the first solve of the batch
  *             (block 128 or 256 x tile 1024, 4096 or 16384 rows;
  *             short timed runs of each candidate on internal buffers; the

@@ -478,7 +478,7 @@ rpcg_status rpcg_batch_solve(rpcg_batch_t B, const double* const* b, double* con
   RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
   RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
-  RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
+  RPCG_CHECK_ARG(opt.tile >= 0 && opt.tile <= (1 << 24), "tile must be 0 (autotuned) or 1..2^24 rows");
   for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   int block = opt.block, tile = opt.tile;
@@ -542,7 +542,7 @@ rpcg_status rpcg_batch_solve_profiled(rpcg_batch_t B, const double* const* b, do
   RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
   RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
-  RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
+  RPCG_CHECK_ARG(opt.tile >= 0 && opt.tile <= (1 << 24), "tile must be 0 (autotuned) or 1..2^24 rows");
   for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   const int block = opt.block ? opt.block : (B->tuned_block ? B->tuned_block : 128);
@@ -577,7 +577,7 @@ rpcg_status rpcg_batch_solve_async(rpcg_batch_t B, const double* const* b, doubl
   RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0) && !std::isnan(opt.tol), "bad tol or max_iter");
   RPCG_CHECK_ARG(opt.fpe_size >= 0 && opt.fpe_size <= kFpeMax, "fpe_size must be 0 (adaptive) or 1..8");
   RPCG_CHECK_ARG(opt.block == 0 || opt.block == 128 || opt.block == 256, "block must be 0, 128 or 256 here");
-  RPCG_CHECK_ARG(opt.tile >= 0, "tile must be >= 0");
+  RPCG_CHECK_ARG(opt.tile >= 0 && opt.tile <= (1 << 24), "tile must be 0 (autotuned) or 1..2^24 rows");
   for (int i = 0; i < B->count; i++) RPCG_CHECK_ARG(B->mats[i]->m.n == 0 || (b[i] && x[i]), "b[i] or x[i] is NULL");
   cudaStream_t s = (cudaStream_t)stream;
   // no autotuning here (it times runs): the tuned shape if there is one, else 128 x 1024

@@ -32,6 +32,7 @@
 namespace rpcg {
 
 constexpr int kMaxPassGrid = 4096;
+constexpr int kMaxRows = (1 << 30) + ((1 << 30) - (1 << 25));  // 2^31 - 2^25
 
 // Grid-reduction scratch of one pass: up to three simultaneous dots.
 struct PassScratch {
@@ -1054,6 +1055,9 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
   RPCG_CHECK_ARG(A_out != nullptr, "A_out is NULL");
   *A_out = nullptr;
   RPCG_CHECK_ARG(n >= 0 && nnz >= 0, "n and nnz must be non-negative");
+  // headroom for the 32-bit row indices of the grid-stride loops (strides up
+  // to 2^21) and the batch's unit products (tiles up to 2^24)
+  RPCG_CHECK_ARG(n <= kMaxRows, "n must be at most 2^31 - 2^25");
   RPCG_CHECK_ARG(rowptr != nullptr, "rowptr is NULL");
   RPCG_CHECK_ARG(nnz == 0 || (col != nullptr && val != nullptr), "col or val is NULL");
   RPCG_CHECK_ARG(ptr_kind == 0 || ptr_kind == 1, "ptr_kind must be 0 (host) or 1 (device)");

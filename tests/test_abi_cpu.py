@@ -50,6 +50,9 @@ def test_invalid_arguments_rejected_without_gpu(rpcg):
     h = ctypes.c_void_p()
     rp = (ctypes.c_int32 * 3)(0, 1, 5)  # rowptr[n] != nnz
     assert L.rpcg_create(ctypes.byref(h), 2, 2, rp, rp, rp, 0, None) == rpcg.ERR_INVALID
+    # rows beyond the documented limit (32-bit index headroom), before any array is read
+    assert L.rpcg_create(ctypes.byref(h), 2 ** 31 - 1, 0, None, None, None, 0, None) == rpcg.ERR_INVALID
+    assert b"at most" in L.rpcg_last_error()
 
 
 def test_library_has_no_cpu_fallback_symbols(rpcg):
