@@ -179,7 +179,7 @@ static void serve_loop(rpcg_server_t S) {
   for (;;) {
     // ---- admission (FIFO: stop at the first request that does not fit yet).
     // A cached matrix is pinned (users + 1) as soon as a request naming it is
-    // admitted; a matrix still to be created is reserved once per round.
+    // admitted; a matrix still to be created is reserved once per admission pass.
     std::vector<std::pair<int, rpcg_server_s::Req>> admitted;
     std::vector<rpcg_matrix_t> victims;
     std::set<rpcg_server_s::MatKey> creating;
@@ -239,7 +239,7 @@ static void serve_loop(rpcg_server_t S) {
       const rpcg_server_s::MatKey key{r.rowptr, r.col, r.val, r.n, r.nnz};
       auto it = S->mats.find(key);
       if (it == S->mats.end()) {
-        // first request of this round naming the matrix: create it (its
+        // first request of this admission pass naming the matrix: create it (its
         // bytes were reserved at admission)
         rpcg_matrix_t h = nullptr;
         const rpcg_status cs = rpcg_create(&h, r.n, r.nnz, r.rowptr, r.col, r.val, 0, s);
@@ -255,9 +255,9 @@ static void serve_loop(rpcg_server_t S) {
         it = S->mats.emplace(key, m).first;
         it->second.users++;
       } else if (creating.count(key)) {
-        it->second.users++;  // created earlier in this round for another request
+        it->second.users++;  // created earlier in this admission pass for another request
       }
-      // (a matrix cached before this round was pinned at admission)
+      // (a matrix cached before this admission pass was pinned at admission)
       it->second.last_use = ++S->clock;
       rpcg_server_s::Slot& sl = S->slots[si];
       sl.used = true;
