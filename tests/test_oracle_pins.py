@@ -217,6 +217,33 @@ def test_fpesum_invariant(oracle_lib):
                 assert sum(map(Fraction, a.tolist()), Fraction(0)) == total
 
 
+def test_fpe_one_product_identities(oracle_lib):
+    """The identities a thread holding one product relies on (Algs. 2-4):
+    Alg. 4 into an empty expansion stores the value whole and carries
+    nothing out; Alg. 3 of the twoprod pair's one-term expansions (r) and
+    (s) is one twosum whose error becomes the second term, lost only when
+    p = 1.  Checked against the oracle's own Algs. 3 and 4 and against
+    rational arithmetic."""
+    rng = random.Random(31)
+    for _ in range(3000):
+        a, b = rand_double(rng, -300, 300), rand_double(rng, -300, 300)
+        r, s = oracle_lib.twoprod(a, b)
+        assert Fraction(r) + Fraction(s) == Fraction(a) * Fraction(b)  # exponents keep the error representable
+        for p in (1, 2, 3, 8):
+            res, err = np.zeros(p), np.zeros(p)
+            assert oracle_lib.fpe_accumulate(res, r) == 0.0 and res[0] == r and not res[1:].any()
+            if s != 0.0:
+                assert oracle_lib.fpe_accumulate(err, s) == 0.0 and err[0] == s
+            lost = oracle_lib.fpesum(res, err)
+            r1, s1 = oracle_lib.twosum(r, s)
+            assert same(res[0], r1)
+            if p >= 2:
+                assert not lost and (same(res[1], s1) or (s1 == 0.0 and res[1] == 0.0))
+                assert Fraction(res[0]) + Fraction(res[1]) == Fraction(a) * Fraction(b)
+            else:
+                assert lost == (s1 != 0.0)
+
+
 @pytest.mark.parametrize("fam", ["a", "c8", "c16"])
 @pytest.mark.parametrize("T", [1, 4, 7])
 def test_fpe_dot_equals_exact_when_flagged(oracle_lib, fam, T):
