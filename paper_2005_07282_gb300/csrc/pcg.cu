@@ -327,9 +327,9 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(MatDev m, const double* __restri
 // 1.01 to 1.51 ms at 256^3).
 constexpr bool kPassAIntShare = true;
 template <int V, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 0) k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w,
-                                                  PassScratch* ws, SolveState* st, const SolveArgs* args,
-                                                  cudaGraphConditionalHandle cond) {
+__global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 0)
+    k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w, PassScratch* ws, SolveState* st,
+             const SolveArgs* args, cudaGraphConditionalHandle cond) {
   extern __shared__ __align__(16) unsigned char smem[];
   unsigned long long* sacc;
   FinalScratch* fs = red_carve<V, 1>(smem, sacc);
