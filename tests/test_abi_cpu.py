@@ -23,6 +23,38 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def _declarations_with_comments():
+    """(name, the comment block that documents it) for every function the
+    header declares: the block right before it, or before the group of
+    declarations it belongs to."""
+    out = []
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if not fn.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", fn)).read()
+        tokens = re.finditer(r"/\*.*?\*/|\b(?:rpcg_status|void|const char \*)\s*(rpcg_[a-z0-9_]+)\s*\([^;]*;", src, flags=re.S)
+        last_comment = None
+        for m in tokens:
+            if m.group(0).startswith("/*"):
+                last_comment = m.group(0)
+            else:
+                out.append((m.group(1), last_comment))
+    return out
+
+
+def test_every_declaration_is_documented_and_cites_the_paper():
+    decls = _declarations_with_comments()
+    assert {n for n, _ in decls} == declared_symbols()
+    for name, comment in decls:
+        assert comment, name
+    # the compute entry points cite the passage that defines their operation
+    cites = re.compile(r"Sec\. \d|Alg\. \d|Fig\. \d|Listing \d")
+    for name, comment in decls:
+        if name in ("rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_solve", "rpcg_batch_solve",
+                    "rpcg_create", "rpcg_eft_twosum", "rpcg_eft_twoprod"):
+            assert cites.search(comment), name
+
+
 def test_library_exports_every_declared_symbol(rpcg):
     L = ctypes.CDLL(rpcg.LIB_PATH)
     missing = [n for n in sorted(declared_symbols()) if not hasattr(L, n)]
