@@ -59,6 +59,8 @@ def _load():
         L.oracle_spmv.argtypes = [i32, P, P, P, P, P, ctypes.c_int]
         L.oracle_pcg_loop_seconds.restype = d
         L.oracle_pcg_loop_seconds.argtypes = []
+        L.oracle_pcg_trace.restype = ctypes.c_int
+        L.oracle_pcg_trace.argtypes = [i32, P, P, P, P, P, ctypes.c_int, d, i32, P, P, P, P]
         L.oracle_pcg.restype = ctypes.c_int
         L.oracle_pcg.argtypes = [i32, P, P, P, P, P, ctypes.c_int, d, i32, P, P, P, P, ctypes.c_int]
         _lib = L
@@ -152,3 +154,26 @@ def pcg(A, b, x0=None, variant: int = EXACT, tol: float = 1e-8, max_iter: int = 
                             _ptr(hist), ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tt), nthreads)
     return dict(x=x, status=st, iterations=it.value, relres=rr.value, tau=tt.value,
                 history=hist[: it.value + 1].copy(), loop_seconds=_load().oracle_pcg_loop_seconds())
+
+
+def pcg_trace(A, b, variant: int = EXACT, tol: float = 0.0, max_iter: int = 2):
+    """oracle_pcg with every loop test recorded (tiny systems): a list of
+    dicts with dw, rho, beta, tau, gamma, relres and the vectors x, r, z, d
+    after the set-up (entry 0) and after each loop body."""
+    b = _f64(b)
+    n = A.n
+    x = np.zeros(n)
+    rec = 6 + 4 * n
+    tr = np.full((max_iter + 1) * rec, np.nan)
+    it, rr, tt = ctypes.c_int32(), ctypes.c_double(), ctypes.c_double()
+    rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+    cl = np.ascontiguousarray(A.col, dtype=np.int32)
+    vl = _f64(A.val)
+    st = _load().oracle_pcg_trace(n, _ptr(rp), _ptr(cl), _ptr(vl), _ptr(b), _ptr(x), variant, tol, max_iter,
+                                  _ptr(tr), ctypes.byref(it), ctypes.byref(rr), ctypes.byref(tt))
+    out = []
+    for l in range(it.value + 1):
+        t = tr[l * rec:(l + 1) * rec]
+        out.append(dict(dw=t[0], rho=t[1], beta=t[2], tau=t[3], gamma=t[4], relres=t[5], x=t[6:6 + n].copy(),
+                        r=t[6 + n:6 + 2 * n].copy(), z=t[6 + 2 * n:6 + 3 * n].copy(), d=t[6 + 3 * n:6 + 4 * n].copy()))
+    return dict(status=st, iterations=it.value, trace=out)

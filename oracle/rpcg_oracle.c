@@ -435,9 +435,30 @@ static double now_seconds(void) {
 static double g_loop_seconds = 0.0;
 double oracle_pcg_loop_seconds(void) { return g_loop_seconds; }
 
-int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b, double *x,
-               int variant, double tol, int32_t max_iter, double *history, int32_t *iterations, double *relres_out,
-               double *tau_out, int nthreads) {
+/* Optional per-loop-test record (for checking every scalar and vector of a
+ * tiny solve against a hand-worked trace): record l holds
+ * [<d,w>, rho, beta, tau, gamma, relres, x[0..n), r[0..n), z[0..n), d[0..n)]
+ * after the set-up (l = 0; <d,w>, rho, gamma are NaN there) and after each
+ * loop body l = 1, 2, ...  It only copies values; no arithmetic. */
+static void trace_record(double *trace, int32_t l, int32_t n, double dw, double rho, double beta, double tau,
+                         double gamma, double rel, const double *x, const double *r, const double *z, const double *d) {
+    if (!trace) return;
+    double *t = trace + (size_t)l * (6 + 4 * (size_t)n);
+    t[0] = dw;
+    t[1] = rho;
+    t[2] = beta;
+    t[3] = tau;
+    t[4] = gamma;
+    t[5] = rel;
+    memcpy(t + 6, x, sizeof(double) * (size_t)n);
+    memcpy(t + 6 + n, r, sizeof(double) * (size_t)n);
+    memcpy(t + 6 + 2 * (size_t)n, z, sizeof(double) * (size_t)n);
+    memcpy(t + 6 + 3 * (size_t)n, d, sizeof(double) * (size_t)n);
+}
+
+static int pcg_core(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b, double *x,
+                    int variant, double tol, int32_t max_iter, double *history, int32_t *iterations, double *relres_out,
+                    double *tau_out, int nthreads, double *trace) {
     g_loop_seconds = 0.0;
     *iterations = 0;
     *relres_out = NAN;
@@ -493,6 +514,7 @@ int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const doubl
     int32_t l = 0;
     double rel = sqrt(tau) / bnorm;
     if (history) history[0] = rel;
+    trace_record(trace, 0, n, NAN, NAN, beta, tau, NAN, rel, x, r, z, d);
     double t_loop = now_seconds();
     while (rel >= tol && l < max_iter) {
         double beta_old = beta;
@@ -527,6 +549,7 @@ int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const doubl
         l++;
         rel = sqrt(tau) / bnorm;
         if (history) history[l] = rel;
+        trace_record(trace, l, n, dw, rho, beta, tau, gamma, rel, x, r, z, d);
         if (tau > 0.0 && !(beta > 0.0)) {
             status = OR_ERR_NOT_SPD;
             break;
@@ -544,4 +567,20 @@ done:
     free(d);
     free(w);
     return status;
+}
+
+int oracle_pcg(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b, double *x,
+               int variant, double tol, int32_t max_iter, double *history, int32_t *iterations, double *relres_out,
+               double *tau_out, int nthreads) {
+    return pcg_core(n, rowptr, col, val, b, x, variant, tol, max_iter, history, iterations, relres_out, tau_out,
+                    nthreads, NULL);
+}
+
+/* oracle_pcg with the per-loop-test record of trace_record: `trace` holds
+ * (max_iter + 1) * (6 + 4 n) doubles. */
+int oracle_pcg_trace(int32_t n, const int32_t *rowptr, const int32_t *col, const double *val, const double *b,
+                     double *x, int variant, double tol, int32_t max_iter, double *trace, int32_t *iterations,
+                     double *relres_out, double *tau_out) {
+    return pcg_core(n, rowptr, col, val, b, x, variant, tol, max_iter, NULL, iterations, relres_out, tau_out, 1,
+                    trace);
 }

@@ -12,6 +12,7 @@ import scipy.sparse
 import scipy.sparse.linalg
 
 import synth
+from conftest import pcg_2x2_golden
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
 OVER = Fraction(2) ** 1024 * (1 - Fraction(1, 2 ** 54))
@@ -200,6 +201,46 @@ def test_fpe_accumulate_invariant(oracle_lib):
             c = oracle_lib.fpe_accumulate(a, x)
             after = sum(map(Fraction, a.tolist()), Fraction(0))
             assert after + Fraction(c) == before + Fraction(x)
+
+
+def _parse_fpesum_golden():
+    for line in open(os.path.join(GOLDEN, "fpesum.txt")):
+        line = line.strip()
+        if not line or line.startswith("#"):
+            continue
+        p, a, b, after, lost = (t.strip() for t in line.split("|"))
+        yield (int(p), [float.fromhex(t) for t in a.split()], [float.fromhex(t) for t in b.split()],
+               [float.fromhex(t) for t in after.split()], bool(int(lost)))
+
+
+def test_fpesum_golden(oracle_lib):
+    """Alg. 3 on multi-term expansions, worked by hand: term order of b,
+    cancellation leaving overlapping terms, and losses at p = 1, 2, 3."""
+    cases = list(_parse_fpesum_golden())
+    assert len(cases) >= 8
+    for p, a, b, after, lost in cases:
+        assert len(a) == len(b) == len(after) == p
+        x = np.array(a, dtype=np.float64)
+        got_lost = oracle_lib.fpesum(x, np.array(b, dtype=np.float64))
+        assert [same(u, v) for u, v in zip(x.tolist(), after)] == [True] * p, (a, b, x.tolist(), after)
+        assert got_lost == lost, (a, b)
+
+
+def test_pcg_2x2_hand_worked_trace(oracle_lib):
+    """Every scalar and vector of two loop bodies (Fig. 1/Fig. 2 with the
+    fma forms of Sec. 4.3) against a trace worked out by hand with exact
+    rational arithmetic.  The system is chosen so that each single-rounding
+    form differs from its two-rounding neighbour somewhere (r, x, d) and the
+    Jacobi multiply by RN(1/a_ii) differs from a division by a_ii."""
+    A, b, want = pcg_2x2_golden()
+    got = oracle_lib.pcg_trace(A, b, tol=0.0, max_iter=2)
+    assert got["status"] == oracle_lib.NOT_CONVERGED and got["iterations"] == 2
+    assert sorted(want) == [0, 1, 2]
+    for l, names in want.items():
+        rec = got["trace"][l]
+        for name, vals in names.items():
+            have = np.atleast_1d(rec[name]).tolist()
+            assert [same(u, v) for u, v in zip(have, vals)] == [True] * len(vals), (l, name, have, vals)
 
 
 def test_fpesum_invariant(oracle_lib):
