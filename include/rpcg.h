@@ -147,31 +147,41 @@ rpcg_status rpcg_dot_exact(int64_t n, const double *a, const double *b, double *
  * allocate device memory: e.g. a framework whose own allocator already
  * holds all of the GPU's memory, or a time-critical loop where an
  * allocation and the synchronisation it may cause are not acceptable.  The
- * paper has no counterpart; this is a deployment variant of Sec. 4.1's dot.
+ * paper has no counterpart.
  *   n         0 <= n <= 2^30 (larger n returns RPCG_ERR_INVALID).
  *   a, b      device arrays of n doubles; out: device pointer to one double.
  * It allocates nothing: its scratch is one fixed 64 KiB array inside the
  * library, which every GPU that loads the library keeps until the process
- * exits.  The first call on each device looks up that array's device
- * address with the device current; make that first call before any stream
- * capture.  All calls on a device share the one array: calls that may
- * overlap on the GPU (on different streams without ordering between them)
- * race and give wrong results; serialise them.  Asynchronous.
+ * exits.  The first call in each CUDA context (normally the device's primary
+ * context; a context created later, e.g. after cudaDeviceReset, counts as a
+ * new one) looks up that array's device address with the context current;
+ * make that first call before any stream capture.  All calls on a device
+ * share the one array, and each call clears the part that must start at
+ * zero: calls that may overlap on the GPU (on different streams without
+ * ordering between them) race and give wrong results; serialise them.
+ * Asynchronous.
  */
 rpcg_status rpcg_dot_exact_noalloc(int64_t n, const double *a, const double *b, double *out, void *stream);
 
 /*
- * rpcg_dot_fpe -- FPE dot of Sec. 4.2 / Listing 2: each thread keeps a
- * result expansion and an error expansion of p terms (Alg. 4 with the early
- * exit, fed by Alg. 2's product and error), the expansions are merged with
- * Alg. 3 in a fixed tree, and the merged expansion is rounded correctly
- * (the value NearSum returns).
+ * rpcg_dot_fpe -- FPE dot of Sec. 4.2: each thread keeps a result expansion
+ * and an error expansion of p terms (Alg. 4 with the early exit, fed by
+ * Alg. 2's product and error) and merges its two expansions with Alg. 3.
+ * The threads' merged expansions are then added exactly: every term goes
+ * into a long accumulator of 64-bit digits (the exact dot's), which is
+ * rounded once to nearest even.  This replaces the paper's fpesum merge
+ * across threads (Listing 2) and its NearSum; the merge itself loses nothing.
  *   p       terms per expansion, 1..8.
- *   out     device pointer to one double.
- *   exact   device pointer to one int32: 1 if no bits were lost (then *out
- *           equals rpcg_dot_exact's value), 0 if an expansion carried a
- *           value out of its last term, a product fell below 2^-969, or a
- *           term became non-finite.
+ *   out     device pointer to one double: the correctly rounded sum of the
+ *           threads' terms (NaN if a term or an input is not finite).
+ *   exact   device pointer to one int32: 1 if no thread's expansion lost
+ *           bits (then *out equals rpcg_dot_exact's value), 0 if a thread's
+ *           Accumulate carried a value out of its last term, a product of
+ *           non-zero operands fell below 2^-969 (twoprod's error may not be
+ *           representable), or a term or an input was not finite.  Only the
+ *           threads' own losses count, so the flag and a lossy *out depend
+ *           on how the elements are spread over threads; when one thread
+ *           holds every product they equal the paper's algorithm exactly.
  * Asynchronous.
  */
 rpcg_status rpcg_dot_fpe(int64_t n, const double *a, const double *b, int32_t p, double *out, int32_t *exact,
@@ -345,9 +355,15 @@ rpcg_status rpcg_solve_batched(int32_t count, const rpcg_matrix_t *A, const doub
  * arrive (continuous batching).  A scheduler thread admits queued requests
  * into a table of `max_slots` slots while the device bytes in use (cached
  * matrices plus the vectors of running systems) stay within the HBM budget;
- * matrices stay on the device in an LRU cache keyed by the host arrays that
- * named them, so repeated requests on the same matrix do not upload it
- * again.  Running systems advance together, 16 iterations per scheduling
+ * matrices stay on the device in an LRU cache, so repeated requests on the
+ * same matrix do not upload it again.  A cached copy is reused only when the
+ * contents are known to be the same: for a matrix registered with
+ * rpcg_server_register (the server holds its own host copy), or for host
+ * arrays submitted while an earlier request on the same addresses is still
+ * uncollected (those arrays must not change until then).  Once every
+ * ticket on some arrays has been collected, their addresses name nothing:
+ * the next submit with them uploads afresh, whatever they now hold.
+ * Running systems advance together, 16 iterations per scheduling
  * step, through the batched passes of rpcg_batch_solve; systems that stop
  * leave and queued ones join between steps.  Every result is bit-identical
  * to rpcg_solve of the same system alone (exact dots).  The paper has no
@@ -360,6 +376,17 @@ rpcg_status rpcg_solve_batched(int32_t count, const rpcg_matrix_t *A, const doub
  *   max_iter from o).  rowptr/col/val (n, nnz) and b, and x0 if not NULL
  *   (else x0 = 0), are host arrays that must stay valid and unchanged until
  *   rpcg_server_wait returns for this ticket.  Never blocks on the GPU.
+ * rpcg_server_register -- copy a CSR matrix (host arrays, n and nnz as
+ *   in rpcg_create) into the server and return its id in *matrix; the
+ *   caller's arrays may be freed when the call returns.  The copy and the
+ *   device copy made from it are kept until rpcg_server_unregister and the
+ *   collection of every ticket on it (the device copy may be evicted under
+ *   the budget and uploaded again from the server's copy).
+ * rpcg_server_submit_registered -- queue one solve on a registered matrix;
+ *   b, and x0 if not NULL, as in rpcg_server_submit.  RPCG_ERR_INVALID for
+ *   an unknown or unregistered id.
+ * rpcg_server_unregister -- release a registered matrix (requests already
+ *   queued on it still run).
  * rpcg_server_wait -- wait up to timeout_us (< 0: forever) for a ticket;
  *   copies x into x_host (n doubles, may be NULL), fills res and, if not
  *   NULL, the time the request queued and the time it was served.  Returns
@@ -387,6 +414,11 @@ rpcg_status rpcg_server_create(rpcg_server_t *srv, size_t hbm_budget_bytes, int3
 rpcg_status rpcg_server_submit(rpcg_server_t srv, int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
                                const double *val, const double *b, const double *x0, int32_t v, const rpcg_opts *o,
                                uint64_t *ticket);
+rpcg_status rpcg_server_register(rpcg_server_t srv, int32_t n, int32_t nnz, const int32_t *rowptr, const int32_t *col,
+                                 const double *val, uint64_t *matrix);
+rpcg_status rpcg_server_submit_registered(rpcg_server_t srv, uint64_t matrix, const double *b, const double *x0,
+                                          int32_t v, const rpcg_opts *o, uint64_t *ticket);
+rpcg_status rpcg_server_unregister(rpcg_server_t srv, uint64_t matrix);
 rpcg_status rpcg_server_wait(rpcg_server_t srv, uint64_t ticket, double *x_host, rpcg_result *res,
                              rpcg_server_timing *timing, int64_t timeout_us);
 rpcg_status rpcg_server_stats(rpcg_server_t srv, rpcg_server_stats_t *st);

@@ -133,7 +133,8 @@ def test_dot_fpe_flag_cases(rpcg, cuda):
 
 def _one_thread(vals_a, vals_b, t, n=2048, nthr=256):
     """Arrays of n pairs whose non-zero products all land in thread t of the
-    FPE dot's single CTA (thread t takes elements t, t + 256, ...)."""
+    FPE dot's single CTA (thread t takes elements t, t + 256, ...; up to
+    n = 4096 the dot runs as one CTA of 256 threads)."""
     a, b = np.zeros(n), np.zeros(n)
     for k, (x, y) in enumerate(zip(vals_a, vals_b)):
         a[t + k * nthr], b[t + k * nthr] = x, y
@@ -166,9 +167,43 @@ def test_dot_fpe_integer_and_fp64_warps_agree(rpcg, cuda, oracle_lib, p):
             v, ex = rpcg.dot_fpe(_dev(a, cuda), _dev(b, cuda), p=p)
             got.append((bits([v.item()])[0] if not math.isnan(v.item()) else "nan", ex.item()))
         assert len(set(got)) == 1, (va, got)
+        # one thread holds every product, so no cross-thread merge happens and
+        # the paper's one-thread FPE dot gives the value and flag, lossy or not
+        a, b = _one_thread(va, vb, 0)
+        want_v, want_ex = oracle_lib.dot_fpe(a, b, p=p, T=1)
+        assert same(v.item(), want_v) and ex.item() == int(want_ex), (va, v.item(), ex.item(), want_v, want_ex)
         if got[0][1] == 1:
-            a, b = _one_thread(va, vb, 0)
             assert same(v.item(), oracle_lib.dot_exact(a, b))
+
+
+@pytest.mark.parametrize("cond", [1e8, 1e24, 1e40])
+@pytest.mark.parametrize("p", [1, 2, 3, 8])
+def test_dot_fpe_one_thread_equals_oracle_fpe(rpcg, cuda, oracle_lib, cond, p):
+    """Sec. 4.2's FPE dot (Algs. 2 and 4 with the early exit, Alg. 3, then the
+    correctly rounded sum of the terms) against the oracle's, value and flag
+    bit for bit, including every case where the expansion loses bits.  All
+    16 products of an ill-conditioned family-(c) input are placed in one
+    thread (of an integer-pipe warp or of an FP64 warp) of the FPE dot's
+    single CTA; every other element is zero.  With one thread the GPU's
+    exact cross-thread merge and the paper's fpesum merge coincide, so the
+    oracle's one-thread dot is the expected result."""
+    va, vb = synth.dot_family_c(16, cond, 3)
+    want_exact = oracle_lib.dot_exact(va, vb)
+    flags = set()
+    for t in (0, 40, 95, 96, 160, 255):
+        a, b = _one_thread(va, vb, t, n=4096)
+        v, ex = rpcg.dot_fpe(_dev(a, cuda), _dev(b, cuda), p=p)
+        want_v, want_ex = oracle_lib.dot_fpe(a, b, p=p, T=1)
+        assert same(v.item(), want_v), (t, v.item(), want_v)
+        assert ex.item() == int(want_ex), (t, ex.item(), want_ex)
+        flags.add(int(want_ex))
+    # the cases cover both outcomes: p = 1 always loses bits on these inputs,
+    # p = 8 never does (then the value is the exact dot)
+    if p == 1:
+        assert flags == {0}
+        assert not same(v.item(), want_exact)
+    if p == 8:
+        assert flags == {1} and same(v.item(), want_exact)
 
 
 def test_dot_plain_close(rpcg, cuda, oracle_lib):
