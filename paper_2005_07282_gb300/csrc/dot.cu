@@ -1,8 +1,12 @@
 // Standalone dot products: exact (long accumulator), FPE with exactness
 // flag, and the plain FP64 baseline; plus the library-wide host helpers.
+#include <cuda.h>  // CUcontext and CUresult types only: driver entry points are fetched at run time
+
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "device.cuh"
 #include "host.h"
@@ -378,29 +382,66 @@ constexpr int64_t kNoAllocMaxN = int64_t(1) << 30;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
-// Device address of g_noalloc_scratch per device, looked up once per device
-// (in host code the array's name is only a stand-in, not a device address).
+// In host code the array's name is only a stand-in, not a device address:
+// its address is looked up with cudaGetSymbolAddress, once per CUDA context
+// (a device's primary context, or another one the caller made current), with
+// that context current.  The cache is keyed by the driver's context ID, which
+// is unique for the life of the process, so a context created after
+// cudaDeviceReset (or a different context on the same device) gets its own
+// lookup instead of a stale address.
+using CtxGetCurrentFn = CUresult (*)(CUcontext*);
+using CtxGetIdFn = CUresult (*)(CUcontext, unsigned long long*);
+
 static std::mutex g_noalloc_mutex;
-static void* g_noalloc_addr[64] = {nullptr};
+static std::vector<std::pair<unsigned long long, void*>> g_noalloc_addr;  // (context ID, device address)
+
+// ID of the current context; false if there is none yet or the driver
+// entry points are unavailable (then nothing is cached).
+static bool current_context_id(unsigned long long* id) {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    void* f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+    cudaGetLastError();
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
 
 static rpcg_status noalloc_scratch(void** out) {
   int dev = 0;
   RPCG_CUDA_TRY(cudaGetDevice(&dev));
-  if (dev < 0 || dev >= 64) {
-    set_error("rpcg_dot_exact_noalloc: device index %d out of range", dev);
-    return RPCG_ERR_INVALID;
-  }
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // device `dev` is current here
-    if (e != cudaSuccess || p == nullptr) {
-      set_error("rpcg_dot_exact_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-      return RPCG_ERR_CUDA;
+  unsigned long long id = 0;
+  const bool have_id = current_context_id(&id);
+  if (have_id) {
+    for (const auto& e : g_noalloc_addr) {
+      if (e.first == id) {
+        *out = e.second;
+        return RPCG_OK;
+      }
     }
-    g_noalloc_addr[dev] = p;
   }
-  *out = g_noalloc_addr[dev];
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);  // with the caller's context current
+  if (e != cudaSuccess || p == nullptr) {
+    set_error("rpcg_dot_exact_noalloc: cudaGetSymbolAddress on device %d failed: %s", dev, cudaGetErrorString(e));
+    return RPCG_ERR_CUDA;
+  }
+  // the lookup creates the primary context if none was current before it
+  if (have_id || current_context_id(&id)) g_noalloc_addr.emplace_back(id, p);
+  *out = p;
   return RPCG_OK;
 }
 

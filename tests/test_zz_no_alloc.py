@@ -40,6 +40,31 @@ def test_noalloc_matches_allocating_exact_dot_twice(rpcg, cuda):
             assert np.float64(got.item()).view(np.int64) == np.float64(ref.item()).view(np.int64)
 
 
+def test_noalloc_empty_and_unaligned_after_a_large_call(rpcg, cuda):
+    """A large call leaves the shared array holding its digits, counter and
+    flags; the calls right after it on the same stream must start clean.
+    n = 0 gives +0, and views offset by one element (not 16-byte aligned,
+    the other instance of the kernel) give rpcg_dot_exact's bits."""
+    import torch
+    a_np, b_np = synth.dot_family_b(2000001, 73)
+    a = torch.from_numpy(a_np).to(cuda)
+    b = torch.from_numpy(b_np).to(cuda)
+    big = torch.empty((), dtype=torch.float64, device=cuda)
+    empty = torch.full((), float("nan"), dtype=torch.float64, device=cuda)
+    got = torch.full((), float("nan"), dtype=torch.float64, device=cuda)
+    ref = torch.empty((), dtype=torch.float64, device=cuda)
+    _call(rpcg, "rpcg_dot_exact_noalloc", a, b, big)
+    _call(rpcg, "rpcg_dot_exact_noalloc", a[:0], b[:0], empty)
+    _call(rpcg, "rpcg_dot_exact_noalloc", a[1:], b[1:], got)
+    _call(rpcg, "rpcg_dot_exact", a[1:], b[1:], ref)
+    torch.cuda.synchronize()
+    assert np.float64(empty.item()).view(np.int64) == 0  # +0, not -0 or NaN
+    assert np.float64(got.item()).view(np.int64) == np.float64(ref.item()).view(np.int64)
+    _call(rpcg, "rpcg_dot_exact", a, b, ref)
+    torch.cuda.synchronize()
+    assert np.float64(big.item()).view(np.int64) == np.float64(ref.item()).view(np.int64)
+
+
 def test_noalloc_rejects_sizes_beyond_its_maximum(rpcg, cuda):
     L = rpcg.lib()
     st = L.rpcg_dot_exact_noalloc((1 << 30) + 1, ctypes.c_void_p(8), ctypes.c_void_p(8), ctypes.c_void_p(8), None)
