@@ -29,7 +29,8 @@ EXPORTS = [
     "rpcg_matrix_info", "rpcg_spmv", "rpcg_dot_exact", "rpcg_dot_fpe", "rpcg_dot_plain", "rpcg_solve",
     "rpcg_solve_host", "rpcg_solve_profiled", "rpcg_solve_path", "rpcg_solve_async", "rpcg_dot_exact_noalloc", "rpcg_batch_create",
     "rpcg_batch_destroy", "rpcg_batch_solve", "rpcg_batch_solve_profiled", "rpcg_batch_solve_async", "rpcg_batch_tuned", "rpcg_solve_batched", "rpcg_server_create",
-    "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_eft_twosum",
+    "rpcg_server_submit", "rpcg_server_wait", "rpcg_server_stats", "rpcg_server_destroy", "rpcg_server_register",
+    "rpcg_server_submit_registered", "rpcg_server_unregister", "rpcg_eft_twosum",
     "rpcg_eft_twoprod",
 ]
 
@@ -113,6 +114,10 @@ def lib():
         L.rpcg_server_create.argtypes = [ctypes.POINTER(P), ctypes.c_size_t, i32]
         L.rpcg_server_submit.argtypes = [P, i32, i32, P, P, P, P, P, i32, ctypes.POINTER(Opts),
                                          ctypes.POINTER(ctypes.c_uint64)]
+        L.rpcg_server_register.argtypes = [P, i32, i32, P, P, P, ctypes.POINTER(ctypes.c_uint64)]
+        L.rpcg_server_submit_registered.argtypes = [P, ctypes.c_uint64, P, P, i32, ctypes.POINTER(Opts),
+                                                    ctypes.POINTER(ctypes.c_uint64)]
+        L.rpcg_server_unregister.argtypes = [P, ctypes.c_uint64]
         L.rpcg_server_wait.argtypes = [P, ctypes.c_uint64, P, ctypes.POINTER(Result), ctypes.POINTER(ServerTiming),
                                        ctypes.c_int64]
         L.rpcg_server_stats.argtypes = [P, ctypes.POINTER(ServerStats)]
@@ -389,6 +394,33 @@ class Server:
         _check(lib().rpcg_server_create(ctypes.byref(self._h), int(hbm_budget_bytes), int(max_slots)),
                "rpcg_server_create")
         self._keep = {}
+        self._sizes = {}
+
+    def register(self, A) -> int:
+        """rpcg_server_register: the server copies A (host CSR); returns its id."""
+        rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
+        cl = np.ascontiguousarray(A.col, dtype=np.int32)
+        vl = np.ascontiguousarray(A.val, dtype=np.float64)
+        m = ctypes.c_uint64()
+        _check(lib().rpcg_server_register(self._h, A.n, int(vl.size), rp.ctypes.data, cl.ctypes.data, vl.ctypes.data,
+                                          ctypes.byref(m)), "rpcg_server_register")
+        self._sizes[m.value] = A.n
+        return m.value
+
+    def unregister(self, matrix: int):
+        _check(lib().rpcg_server_unregister(self._h, matrix), "rpcg_server_unregister")
+
+    def submit_registered(self, matrix: int, b: np.ndarray, x0=None, tol=1e-8, max_iter=1000) -> int:
+        """rpcg_server_submit_registered: a solve on a registered matrix."""
+        b = np.ascontiguousarray(b, dtype=np.float64)
+        x0 = None if x0 is None else np.ascontiguousarray(x0, dtype=np.float64)
+        o = make_opts(tol=tol, max_iter=max_iter)
+        t = ctypes.c_uint64()
+        _check(lib().rpcg_server_submit_registered(self._h, matrix, b.ctypes.data,
+                                                   None if x0 is None else x0.ctypes.data, EXBLAS, ctypes.byref(o),
+                                                   ctypes.byref(t)), "rpcg_server_submit_registered")
+        self._keep[t.value] = (b, x0, self._sizes[matrix])
+        return t.value
 
     def submit(self, A, b: np.ndarray, x0=None, tol=1e-8, max_iter=1000) -> int:
         rp = np.ascontiguousarray(A.rowptr, dtype=np.int32)
@@ -406,7 +438,7 @@ class Server:
 
     def wait(self, ticket: int, timeout_us: int = -1):
         """Returns (x, result dict with queue_us/service_us)."""
-        n = self._keep[ticket][5] if ticket in self._keep else 0
+        n = self._keep[ticket][-1] if ticket in self._keep else 0
         x = np.empty(n, dtype=np.float64)
         r = Result()
         tm = ServerTiming()
@@ -431,6 +463,7 @@ class Server:
             lib().rpcg_server_destroy(self._h)
             self._h = ctypes.c_void_p()
         self._keep = {}
+        self._sizes = {}
 
     def __del__(self):
         try:

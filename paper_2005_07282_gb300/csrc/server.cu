@@ -3,13 +3,24 @@
 // Requests (CSR + b in host memory) enter a FIFO queue.  A scheduler thread
 // owns the GPU side: it admits requests into a fixed table of slots while a
 // slot is free and the device bytes in use stay within the HBM budget,
-// keeps every matrix it has seen on the device in an LRU cache (requests
-// naming the same host arrays share one device copy; each slot has its own
-// b, x and Krylov vectors), runs the set-up pass for newly admitted
-// systems, and then a chunk of kChunk iterations of the batched passes over
-// every system still iterating.  Between chunks it retires the systems that
-// stopped (copying x back to the host) and admits new requests, so work that
-// arrives while others run joins the batch at the next chunk boundary.
+// keeps matrices on the device in an LRU cache (requests on the same matrix
+// share one device copy; each slot has its own b, x and Krylov vectors),
+// runs the set-up pass for newly admitted systems, and then a chunk of
+// kChunk iterations of the batched passes over every system still
+// iterating.  Between chunks it retires the systems that stopped (copying x
+// back to the host) and admits new requests, so work that arrives while
+// others run joins the batch at the next chunk boundary.
+//
+// A cached device copy is only ever reused for a request whose matrix is
+// known to have the same contents.  Every request names a "generation": a
+// matrix registered with rpcg_server_register (the server keeps its own
+// host copy, so its contents cannot change), or host arrays passed to
+// rpcg_server_submit.  Arrays passed to submit must stay unchanged until
+// that ticket is collected, so a request submitted while an earlier request
+// on the same addresses is still uncollected sees the same contents and
+// joins its generation; once every ticket of a generation has been
+// collected the caller may have reused the memory, the addresses stop
+// naming it, and its device copy is freed.
 //
 // Each system goes through exactly the arithmetic of rpcg_solve with the
 // exact dots, so its result is bit-identical to solving it alone, whatever
@@ -56,13 +67,26 @@ struct rpcg_server_s {
     double tol;
     int max_iter;
     double t_submit;
+    uint64_t gen;  // the matrix generation this request solves with
   };
   struct Done {
     rpcg_result res;
     std::vector<double> x;
     double queue_us, service_us;
   };
-  using MatKey = std::tuple<const void*, const void*, const void*, int, int>;
+  // host arrays of a submit request, and the generation they name while
+  // some request on them is uncollected
+  using AddrKey = std::tuple<const void*, const void*, const void*, int, int>;
+  struct Gen {
+    int holders = 0;      // uncollected tickets, plus one while registered
+    bool has_addr = false;
+    bool registered = false;  // held by rpcg_server_register until rpcg_server_unregister
+    AddrKey addr{};
+    // a registered matrix: the server's own copy of the CSR arrays
+    std::vector<int> rowptr, col;
+    std::vector<double> val;
+  };
+  using MatKey = uint64_t;  // generation id
   struct Mat {
     rpcg_matrix_t h = nullptr;
     size_t bytes = 0;
@@ -90,11 +114,18 @@ struct rpcg_server_s {
   std::deque<Req> queue;
   std::unordered_map<uint64_t, Done> done;
   std::map<uint64_t, int> pending;  // tickets not yet completed (queued or running)
+  std::unordered_map<uint64_t, uint64_t> ticket_gen;  // uncollected ticket -> generation
+  std::unordered_map<uint64_t, Gen> gens;             // live generations
+  std::map<AddrKey, uint64_t> addr_gen;              // submit arrays -> their live generation
+  std::vector<uint64_t> dead_gens;                    // no ticket can name these again
+  uint64_t next_gen = 1;
+
+  // device cache and byte count (read by rpcg_server_stats; guarded by mu)
+  std::map<MatKey, Mat> mats;
+  size_t used_bytes = 0;
 
   // scheduler thread only
-  std::map<MatKey, Mat> mats;
   std::vector<Slot> slots;
-  size_t used_bytes = 0;
   uint64_t clock = 0;
   rpcg::SysDev* d_sys = nullptr;
   rpcg::SysDev* h_sys = nullptr;
@@ -124,6 +155,22 @@ static size_t slot_bytes(int n) { return (size_t)6 * (size_t)(n > 0 ? n : 1) * s
 static size_t mat_bytes(int n, int nnz) {
   return (size_t)((double)nnz * 12.0 * 1.05) + (size_t)4 * (n + 1) + (size_t)8 * (n / 32 + 2) + slot_bytes(n) +
          (size_t)(256 << 10);
+}
+
+// Drop one hold on a generation (S->mu held).  At zero no ticket names it
+// and none can again: its addresses are forgotten, a registered copy is
+// freed, and the scheduler frees the device copy.
+static void release_gen(rpcg_server_t S, uint64_t g) {
+  auto it = S->gens.find(g);
+  if (it == S->gens.end()) return;
+  if (--it->second.holders > 0) return;
+  if (it->second.has_addr) {
+    auto a = S->addr_gen.find(it->second.addr);
+    if (a != S->addr_gen.end() && a->second == g) S->addr_gen.erase(a);
+  }
+  S->gens.erase(it);
+  S->dead_gens.push_back(g);
+  S->cv_work.notify_one();
 }
 
 static void complete(rpcg_server_t S, uint64_t ticket, const rpcg_result& res, std::vector<double>&& x, double qus,
@@ -182,13 +229,28 @@ static void serve_loop(rpcg_server_t S) {
     // admitted; a matrix still to be created is reserved once per admission pass.
     std::vector<std::pair<int, rpcg_server_s::Req>> admitted;
     std::vector<rpcg_matrix_t> victims;
-    std::set<rpcg_server_s::MatKey> creating;
+    std::set<rpcg_server_s::MatKey> creating;  // matrix bytes reserved in this pass, not created yet
+    std::set<rpcg_server_s::MatKey> created;   // created in this pass
     {
       std::unique_lock<std::mutex> lock(S->mu);
+      // device copies of generations no ticket can name again
+      for (const uint64_t g : S->dead_gens) {
+        auto it = S->mats.find(g);
+        if (it != S->mats.end() && it->second.users == 0) {
+          victims.push_back(it->second.h);
+          S->used_bytes -= it->second.bytes;
+          S->mats.erase(it);
+        }
+      }
+      S->dead_gens.clear();
       if (running.empty() && S->queue.empty()) {
         if (S->stop) break;
-        S->cv_work.wait_for(lock, std::chrono::milliseconds(50));
-        if (S->queue.empty()) continue;
+        if (victims.empty()) S->cv_work.wait_for(lock, std::chrono::milliseconds(50));
+        if (S->queue.empty()) {
+          lock.unlock();
+          for (rpcg_matrix_t h : victims) rpcg_destroy(h);
+          continue;
+        }
       }
       while (!S->queue.empty()) {
         int free_slot = -1;
@@ -202,7 +264,7 @@ static void serve_loop(rpcg_server_t S) {
         }
         if (free_slot < 0) break;
         const rpcg_server_s::Req r = S->queue.front();
-        const rpcg_server_s::MatKey key{r.rowptr, r.col, r.val, r.n, r.nnz};
+        const rpcg_server_s::MatKey key = r.gen;
         const bool cached = S->mats.count(key) > 0;
         const bool known = cached || creating.count(key) > 0;
         const size_t need = slot_bytes(r.n) + (known ? 0 : mat_bytes(r.n, r.nnz));
@@ -236,29 +298,49 @@ static void serve_loop(rpcg_server_t S) {
       const int si = a.first;
       const rpcg_server_s::Req& r = a.second;
       const double t_admit = now_us();
-      const rpcg_server_s::MatKey key{r.rowptr, r.col, r.val, r.n, r.nnz};
-      auto it = S->mats.find(key);
-      if (it == S->mats.end()) {
-        // first request of this admission pass naming the matrix: create it (its
-        // bytes were reserved at admission)
-        rpcg_matrix_t h = nullptr;
+      const rpcg_server_s::MatKey key = r.gen;
+      rpcg_matrix_t h = nullptr;
+      bool have = false;
+      {
+        std::lock_guard<std::mutex> lock(S->mu);
+        auto it = S->mats.find(key);
+        if (it != S->mats.end()) {
+          // created earlier in this admission pass for another request; (a
+          // matrix cached before this pass was pinned at admission)
+          if (created.count(key)) it->second.users++;
+          it->second.last_use = ++S->clock;
+          h = it->second.h;
+          have = true;
+        }
+      }
+      if (!have) {
+        // first request of this admission pass naming the matrix: create it
+        // (its bytes were reserved at admission); the generation's arrays stay
+        // unchanged while this request is uncollected
         const rpcg_status cs = rpcg_create(&h, r.n, r.nnz, r.rowptr, r.col, r.val, 0, s);
+        {
+          std::lock_guard<std::mutex> lock(S->mu);
+          // the matrix bytes were reserved by the request that admitted the
+          // generation in this pass; if that one failed, this one takes them
+          const bool reserved = creating.erase(key) > 0;
+          if (cs != RPCG_OK) {
+            S->used_bytes -= slot_bytes(r.n) + (reserved ? mat_bytes(r.n, r.nnz) : 0);
+          } else {
+            if (!reserved) S->used_bytes += mat_bytes(r.n, r.nnz);
+            created.insert(key);
+            rpcg_server_s::Mat m;
+            m.h = h;
+            m.bytes = mat_bytes(r.n, r.nnz);
+            m.users = 1;
+            m.last_use = ++S->clock;
+            S->mats.emplace(key, m);
+          }
+        }
         if (cs != RPCG_OK) {
-          S->used_bytes -= slot_bytes(r.n) + mat_bytes(r.n, r.nnz);
-          creating.erase(key);
           fail_req(S, r, cs, t_admit);
           continue;
         }
-        rpcg_server_s::Mat m;
-        m.h = h;
-        m.bytes = mat_bytes(r.n, r.nnz);
-        it = S->mats.emplace(key, m).first;
-        it->second.users++;
-      } else if (creating.count(key)) {
-        it->second.users++;  // created earlier in this admission pass for another request
       }
-      // (a matrix cached before this admission pass was pinned at admission)
-      it->second.last_use = ++S->clock;
       rpcg_server_s::Slot& sl = S->slots[si];
       sl.used = true;
       sl.req = r;
@@ -278,12 +360,14 @@ static void serve_loop(rpcg_server_t S) {
         if (sl.buf) cudaFreeAsync(sl.buf, s);
         sl.buf = nullptr;
         sl.used = false;
-        it->second.users--;
-        S->used_bytes -= sl.bytes;
+        {
+          std::lock_guard<std::mutex> lock(S->mu);
+          S->mats[key].users--;
+          S->used_bytes -= sl.bytes;
+        }
         fail_req(S, r, RPCG_ERR_CUDA, t_admit);
         continue;
       }
-      const rpcg_matrix_t h = it->second.h;
       S->h_sys[si] = SysDev{h->m, B, B + n, B + 2 * (size_t)n, B + 3 * (size_t)n, B + 4 * (size_t)n,
                             B + 5 * (size_t)n, nullptr, r.tol, r.max_iter, 0};
       fresh.push_back(si);
@@ -367,8 +451,11 @@ static void serve_loop(rpcg_server_t S) {
       cudaFreeAsync(sl.buf, s);
       sl.buf = nullptr;
       sl.used = false;
-      S->mats[sl.key].users--;
-      S->used_bytes -= sl.bytes;
+      {
+        std::lock_guard<std::mutex> lock(S->mu);
+        S->mats[sl.key].users--;
+        S->used_bytes -= sl.bytes;
+      }
       complete(S, sl.req.ticket, res, std::move(x), sl.t_admit - sl.req.t_submit, now_us() - sl.t_admit);
     }
     running.swap(still);
@@ -468,12 +555,99 @@ rpcg_status rpcg_server_submit(rpcg_server_t S, int32_t n, int32_t nnz, const in
   {
     std::lock_guard<std::mutex> lock(S->mu);
     RPCG_CHECK_ARG(!S->stop, "server is shutting down");
+    // the arrays name a live generation while a request on them is
+    // uncollected (their contents are unchanged since it was submitted)
+    const rpcg_server_s::AddrKey ak{rowptr, col, val, n, nnz};
+    auto a = S->addr_gen.find(ak);
+    if (a != S->addr_gen.end()) {
+      r.gen = a->second;
+    } else {
+      r.gen = S->next_gen++;
+      rpcg_server_s::Gen& G = S->gens[r.gen];
+      G.has_addr = true;
+      G.addr = ak;
+      S->addr_gen[ak] = r.gen;
+    }
+    S->gens[r.gen].holders++;
     r.ticket = S->next_ticket++;
     S->queue.push_back(r);
     S->pending[r.ticket] = 1;
+    S->ticket_gen[r.ticket] = r.gen;
     *ticket = r.ticket;
   }
   S->cv_work.notify_one();
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_server_register(rpcg_server_t S, int32_t n, int32_t nnz, const int32_t* rowptr, const int32_t* col,
+                                 const double* val, uint64_t* matrix) {
+  clear_error();
+  RPCG_CHECK_ARG(S != nullptr && matrix != nullptr, "server or matrix is NULL");
+  RPCG_CHECK_ARG(n >= 0 && nnz >= 0 && rowptr != nullptr, "bad matrix arrays");
+  RPCG_CHECK_ARG(nnz == 0 || (col != nullptr && val != nullptr), "col or val is NULL");
+  RPCG_CHECK_ARG(rowptr[0] == 0 && rowptr[n] == nnz, "rowptr[0] must be 0 and rowptr[n] must be nnz");
+  rpcg_server_s::Gen G;
+  G.registered = true;
+  G.holders = 1;
+  G.rowptr.assign(rowptr, rowptr + (size_t)n + 1);
+  G.col.assign(col, col + (size_t)nnz);
+  G.val.assign(val, val + (size_t)nnz);
+  std::lock_guard<std::mutex> lock(S->mu);
+  RPCG_CHECK_ARG(!S->stop, "server is shutting down");
+  const uint64_t g = S->next_gen++;
+  S->gens.emplace(g, std::move(G));
+  *matrix = g;
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_server_submit_registered(rpcg_server_t S, uint64_t matrix, const double* b, const double* x0, int32_t v,
+                                          const rpcg_opts* o, uint64_t* ticket) {
+  clear_error();
+  RPCG_CHECK_ARG(S != nullptr && ticket != nullptr, "server or ticket is NULL");
+  RPCG_CHECK_ARG(v == RPCG_EXBLAS, "the serving loop runs the exblas variant");
+  rpcg_opts opt;
+  if (o) opt = *o;
+  else rpcg_opts_default(&opt);
+  RPCG_CHECK_ARG(opt.max_iter >= 0 && !(opt.tol < 0.0), "bad tol or max_iter");
+  {
+    std::lock_guard<std::mutex> lock(S->mu);
+    RPCG_CHECK_ARG(!S->stop, "server is shutting down");
+    auto it = S->gens.find(matrix);
+    RPCG_CHECK_ARG(it != S->gens.end() && it->second.registered, "unknown or unregistered matrix id");
+    rpcg_server_s::Gen& G = it->second;
+    const int n = (int)G.rowptr.size() - 1;
+    RPCG_CHECK_ARG(n == 0 || b != nullptr, "b is NULL");
+    rpcg_server_s::Req r{};
+    r.n = n;
+    r.nnz = (int)G.val.size();
+    r.rowptr = G.rowptr.data();
+    r.col = G.col.data();
+    r.val = G.val.data();
+    r.b = b;
+    r.x0 = x0;
+    r.tol = opt.tol;
+    r.max_iter = opt.max_iter;
+    r.t_submit = now_us();
+    r.gen = matrix;
+    G.holders++;
+    r.ticket = S->next_ticket++;
+    S->queue.push_back(r);
+    S->pending[r.ticket] = 1;
+    S->ticket_gen[r.ticket] = matrix;
+    *ticket = r.ticket;
+  }
+  S->cv_work.notify_one();
+  return RPCG_OK;
+}
+
+rpcg_status rpcg_server_unregister(rpcg_server_t S, uint64_t matrix) {
+  clear_error();
+  RPCG_CHECK_ARG(S != nullptr, "server is NULL");
+  std::lock_guard<std::mutex> lock(S->mu);
+  auto it = S->gens.find(matrix);
+  RPCG_CHECK_ARG(it != S->gens.end() && it->second.registered, "unknown or unregistered matrix id");
+  it->second.registered = false;
+  release_gen(S, matrix);
   return RPCG_OK;
 }
 
@@ -500,6 +674,14 @@ rpcg_status rpcg_server_wait(rpcg_server_t S, uint64_t ticket, double* x_host, r
     timing->service_us = it->second.service_us;
   }
   S->done.erase(it);
+  // the ticket is collected: its hold on the matrix generation ends (the
+  // caller may now change or free the arrays it submitted)
+  auto tg = S->ticket_gen.find(ticket);
+  if (tg != S->ticket_gen.end()) {
+    const uint64_t g = tg->second;
+    S->ticket_gen.erase(tg);
+    release_gen(S, g);
+  }
   return (rpcg_status)res->status;
 }
 

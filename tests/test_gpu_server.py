@@ -111,3 +111,69 @@ def test_server_budget_and_errors(rpcg, cuda):
     x, r = srv.wait(tb, timeout_us=120_000_000)
     assert r["status"] in (0, rpcg.NOT_CONVERGED)
     srv.close()
+
+
+def _wait_cached(srv, want, limit_s=10.0):
+    """Poll the server's cache size until it reaches `want` (the scheduler
+    frees the device copy of a matrix no ticket can name any more)."""
+    t0 = time.time()
+    while srv.stats()["matrices_cached"] != want and time.time() - t0 < limit_s:
+        time.sleep(0.002)
+    return srv.stats()["matrices_cached"]
+
+
+def test_server_arrays_overwritten_after_collection_are_not_served_stale(rpcg, cuda):
+    """The caller may change its arrays once a ticket is collected.  A new
+    matrix written into the same host buffers (same shape, same addresses)
+    must be solved as that new matrix: bit-identical to solving it alone,
+    never the old device copy."""
+    A = synth.poisson7(12)
+    diag = np.array([k for i in range(A.n) for k in range(A.rowptr[i], A.rowptr[i + 1]) if A.col[k] == i])
+    val_ptr = A.val.ctypes.data
+    b = synth.rhs_uniform(A.n, 77)
+    srv = rpcg.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    x1, r1 = srv.wait(srv.submit(A, b, tol=1e-10, max_iter=2000), timeout_us=60_000_000)
+    assert r1["status"] == 0
+    # nothing can name the first matrix any more: its device copy is freed
+    assert _wait_cached(srv, 0) == 0
+    # overwrite the values in place: diagonal 6 -> 8.5, off-diagonals -1 -> -1.25
+    # (still diagonally dominant, so SPD)
+    A.val[:] = -1.25
+    A.val[diag] = 8.5
+    assert A.val.ctypes.data == val_ptr
+    x2, r2 = srv.wait(srv.submit(A, b, tol=1e-10, max_iter=2000), timeout_us=60_000_000)
+    srv.close()
+    ra, xa = _alone(rpcg, cuda, A, b, tol=1e-10)
+    assert r2["status"] == ra["status"] == 0
+    assert r2["iterations"] == ra["iterations"]
+    assert np.array_equal(bits(x2), bits(xa))
+    assert not np.array_equal(bits(x2), bits(x1))
+
+
+def test_server_registered_matrix(rpcg, cuda):
+    """A registered matrix is copied by the server: the caller's arrays can
+    change at once, requests on it share one device copy, and each result is
+    bit-identical to solving the registered matrix alone."""
+    A = synth.poisson7(10)
+    keep = synth.CSR(A.n, A.rowptr.copy(), A.col.copy(), A.val.copy(), A.name)
+    srv = rpcg.Server(hbm_budget_bytes=1 << 30, max_slots=4)
+    m = srv.register(A)
+    A.val[:] = np.nan  # the server holds its own copy
+    bs = [synth.rhs_uniform(keep.n, 600 + k) for k in range(4)]
+    ts = [srv.submit_registered(m, b, tol=1e-9, max_iter=2000) for b in bs]
+    outs = [srv.wait(t, timeout_us=60_000_000) for t in ts]
+    assert srv.stats()["matrices_cached"] == 1
+    # later requests reuse the cached copy after the earlier ones were collected
+    x5, r5 = srv.wait(srv.submit_registered(m, bs[0], tol=1e-9, max_iter=2000), timeout_us=60_000_000)
+    srv.unregister(m)
+    with pytest.raises(rpcg.RpcgError):
+        srv.submit_registered(m, bs[0])
+    with pytest.raises(rpcg.RpcgError):
+        srv.unregister(m)
+    assert _wait_cached(srv, 0) == 0
+    srv.close()
+    for b, (x, r) in zip(bs, outs):
+        ra, xa = _alone(rpcg, cuda, keep, b, tol=1e-9)
+        assert r["status"] == ra["status"] == 0 and r["iterations"] == ra["iterations"]
+        assert np.array_equal(bits(x), bits(xa))
+    assert np.array_equal(bits(x5), bits(outs[0][0])) and r5["iterations"] == outs[0][1]["iterations"]
