@@ -190,9 +190,10 @@ rpcg_status rpcg_dot_fpe(int64_t n, const double *a, const double *b, int32_t p,
 /*
  * rpcg_eft_twosum / rpcg_eft_twoprod -- the error-free transformations of
  * Alg. 1 (r = RN(a_i + b_i), s = a_i + b_i - r) and Alg. 2 (r = RN(a_i b_i),
- * s = fma(a_i, b_i, -r)) applied elementwise.  Finite non-zero elements are
- * computed exactly on the integer pipe (the FPE dot's arithmetic); zero,
- * non-finite or out-of-range elements use the FP64 formulas; every output
+ * s = fma(a_i, b_i, -r)) applied elementwise, with the FPE dot's own
+ * arithmetic: twosum of finite elements as exact integer arithmetic on the
+ * bit patterns (elements that are not finite, or whose sum overflows, use
+ * the FP64 formulas), twoprod as the two FP64 operations.  Every output
  * equals the FP64 algorithm's bit for bit.
  *   a, b      device arrays of n doubles (inputs); r, s: device outputs.
  * Asynchronous.

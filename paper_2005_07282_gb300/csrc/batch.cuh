@@ -19,7 +19,6 @@
 #include <type_traits>
 
 #include "device.cuh"
-#include "softeft.cuh"
 #include "solver.cuh"
 
 namespace rpcg {
@@ -197,15 +196,14 @@ __host__ __device__ constexpr size_t b_smem(int nacc, int count) {
 // row2_fn(ctx, ra, rb, dep) does rows ra and rb together (both in range);
 // pass a NullRow2 to process rows one at a time.  skip_fn(sys) == true
 // skips a system's units altogether (no deposit, no arrival, no fin_fn).
-// kIntShare (fpe): a share of the warps run the element steps on the
-// integer pipes (fpe_int_warp); it pays in kernels light enough for 32
-// warps per SM (measured: the split FPE pass B), not in pass A.
+// fpe: twoprod in FP64, the Accumulate cascades with two_sum_split (one FP64
+// addition per twosum, the error on the integer pipe).
 struct NullRow2 {};
 struct NoSkip {
   __device__ bool operator()(int) const { return false; }
 };
 
-template <int V, int NACC, int BLOCK, bool kIntShare = false, class CtxFn, class PfFn, class RowFn, class FinFn,
+template <int V, int NACC, int BLOCK, class CtxFn, class PfFn, class RowFn, class FinFn,
           class Row2Fn = NullRow2, class SkipFn = NoSkip>
 __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restrict__ prefix, unsigned int* work,
                                           unsigned char* smem, CtxFn ctx_fn, PfFn pf_fn, RowFn row_fn,
@@ -293,11 +291,9 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         smem_acc_zero(sacc, NACC);
         __syncthreads();
         const int r0 = k0 * B.tile, r1 = min(n, k1 * B.tile);
-        const bool int_warp = kIntShare && fpe_int_warp();
         auto dep = [&](int j, double x, double y) {
           if (!is_finite_bits(x) || !is_finite_bits(y)) bad = true;
-          else if (int_warp) lost[j] |= fpe_dot_step_int(res[j], err[j], p, x, y, bad);
-          else lost[j] |= fpe_dot_step(res[j], err[j], p, x, y);
+          else lost[j] |= fpe_dot_step(res[j], err[j], p, x, y, bad);
         };
         for (int row = r0 + threadIdx.x; row < r1; row += (kPair ? 2 : 1) * BLOCK) {
           const int ahead = row + kPfSteps * BLOCK;
@@ -311,7 +307,7 @@ __device__ __forceinline__ void for_units(const BatchDesc& B, const int* __restr
         }
 #pragma unroll
         for (int j = 0; j < NACC; j++) {
-          lost[j] |= fpe_sum(res[j], err[j], p);
+          lost[j] |= fpe_sum(res[j], err[j], p, bad);
           if (lost[j]) atomicOr(&R->flags, 2u << j);
           Window win;
           window_init(win);
@@ -693,13 +689,12 @@ __global__ void __launch_bounds__(BLOCK) k_b_pass_b(BatchDesc B) {
 }
 
 // FPE variant: pass B as two passes, so that each thread holds one pair of
-// expansions (64 registers, a share of the warps on the integer pipes), as
-// in the single-system solve.  B1: S3-S6 (<z,r>, kept in the system's
+// expansions (64 registers), as in the single-system solve.  B1: S3-S6 (<z,r>, kept in the system's
 // state); B2: S8 (<r,r> of the new r) and the finalisation of both dots.
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_b1(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
-  for_units<RPCG_FPE, 1, BLOCK, true>(
+  for_units<RPCG_FPE, 1, BLOCK>(
       B, B.aprefix, &B.head->work[kWorkB], smem,
       [&](int s) {
         const SysDev& S = B.sys[s];
@@ -726,7 +721,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_b1(BatchDesc B) 
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_b_pass_b2(BatchDesc B) {
   extern __shared__ __align__(16) unsigned char smem[];
-  for_units<RPCG_FPE, 1, BLOCK, true>(
+  for_units<RPCG_FPE, 1, BLOCK>(
       B, B.aprefix, &B.head->work[kWorkB2], smem,
       [&](int s) {
         const SysDev& S = B.sys[s];

@@ -19,8 +19,9 @@
 // order-independent, the single-GPU form of Listing 3's MPI_Reduce); the
 // last CTA normalises the carries and rounds once (Round in Listing 3).
 //
-// FPE dot (Sec. 4.2).  twosum (Alg. 1), twoprod (Alg. 2), Accumulate with
-// early exit (Alg. 4) and fpesum (Alg. 3) in FP64.
+// FPE dot (Sec. 4.2).  twoprod (Alg. 2) in FP64; twosum (Alg. 1) in FP64
+// or as exact integer arithmetic on the bit patterns; Accumulate with early
+// exit (Alg. 4) and fpesum (Alg. 3) built on either twosum.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -452,6 +453,191 @@ __device__ __forceinline__ void two_sum_ordered(double a, double b, double& r, d
   s = __dsub_rn(small, z);
 }
 
+// Binary64 bits (sign clear) of m * 2^lsb, for m < 2^56 exactly representable
+// at or above 2^-1074 and lsb >= -1074: normalise m to 53 bits (right
+// shifts drop only zero bits), or stop at 2^-1074 (subnormal).  Adding the
+// shifted significand to (lsb' + 1074) << 52 lets its hidden bit carry into
+// the exponent field, so normal and subnormal values take the same formula.
+// ovf is set if the value is 2^1024 or more.  m = 0 gives +0.
+__device__ __forceinline__ unsigned long long pack_bits(unsigned long long m, int lsb, bool& ovf) {
+  const int nb = 64 - __clzll((long long)m);
+  int shift = 53 - nb;
+  int lsb2 = lsb - shift;
+  if (lsb2 < -1074) {
+    shift = lsb + 1074;
+    lsb2 = -1074;
+  }
+  const unsigned long long mm = shift >= 0 ? (m << shift) : (m >> (-shift));
+  ovf |= (m != 0ull) & (lsb2 >= 972);
+  return m ? ((unsigned long long)(lsb2 + 1074) << 52) + mm : 0ull;
+}
+
+// Alg. 1 on the integer pipe, every case, for finite a and b: r = RN(a + b) and
+// s = a + b - r, the same unique pair as the FP64 formulas (zero terms may
+// differ in sign, which changes no sum).  Let |A| >= |B| be the operands
+// ordered by magnitude, with significands mA, mB and last-bit exponents
+// (B's is the unit below).  If their exponent fields differ by d > 54,
+// |B| < ulp(A)/4: r = A, s = B.  Otherwise B is split at k = max(d - 3, 0)
+// bits into a high part and a low part L < 2^k, so that
+// |A + B| = Mh 2^k + Ml with Mh = mA 2^(d-k) +- high part (below 2^57, three
+// guard bits) and 0 <= Ml < 2^k (a borrow turns a subtracted low part into
+// a positive one): everything fits 64-bit integers.  Mh is rounded to 53
+// bits, ties to even, with Ml as the sticky part; the dropped bits minus
+// the rounding increment, times 2^k, plus Ml, are s.  ovf is set if |r|
+// reaches 2^1024 (the FP64 formulas give a non-finite r there).
+struct TwoSumOut {
+  double r, s;
+  bool ovf;
+};
+
+__device__ __forceinline__ TwoSumOut two_sum_int_general_body(double a, double b) {
+  bool ovf = false;
+  constexpr unsigned long long kAbs = 0x7FFFFFFFFFFFFFFFull, kM52 = 0xFFFFFFFFFFFFFull;
+  const unsigned long long ua = (unsigned long long)__double_as_longlong(a);
+  const unsigned long long ub = (unsigned long long)__double_as_longlong(b);
+  const bool sw = (ub & kAbs) > (ua & kAbs);
+  const unsigned long long A = sw ? ub : ua, B = sw ? ua : ub;
+  const unsigned long long xa = A & kAbs, xb = B & kAbs;
+  const int EA = (int)(xa >> 52), EB = (int)(xb >> 52);
+  const unsigned long long mA = (xa & kM52) | ((unsigned long long)(EA != 0) << 52);
+  const unsigned long long mB = (xb & kM52) | ((unsigned long long)(EB != 0) << 52);
+  const int eB = max(EB, 1);
+  const int d = max(EA, 1) - eB;  // >= 0
+  const bool opp = (long long)(A ^ B) < 0;
+  const int k = min(max(d - 3, 0), 51);  // (clamped only on the d > 54 path, whose values are not used)
+  const unsigned long long mBh = mB >> k, mBl = mB & ((1ull << k) - 1ull);
+  const unsigned long long Ah = mA << min(d, 3);
+  const unsigned long long br = (opp && mBl != 0ull) ? 1ull : 0ull;
+  const unsigned long long Mh = opp ? Ah - mBh - br : Ah + mBh;
+  const unsigned long long Ml = opp ? (br ? (1ull << k) - mBl : 0ull) : mBl;
+  const int nb = 64 - __clzll((long long)Mh);
+  const int sh = max(nb - 53, 0);
+  const unsigned long long q0 = Mh >> sh;
+  const unsigned long long low = Mh & ((1ull << sh) - 1ull);
+  const unsigned long long half = (1ull << sh) >> 1;
+  const bool up = sh != 0 && (low > half || (low == half && (Ml != 0ull || (q0 & 1ull))));
+  const unsigned long long q = q0 + (up ? 1ull : 0ull);
+  // s in units of B's last bit, as a two's-complement 64-bit value (|s| < 2^56)
+  const unsigned long long sv = ((low - (up ? (1ull << sh) : 0ull)) << k) + Ml;
+  const bool sneg = (long long)sv < 0;
+  const unsigned long long smag = sneg ? 0ull - sv : sv;
+  const unsigned long long signA = A & ~kAbs;
+  bool o = false;
+  const unsigned long long rb = q ? (pack_bits(q, eB - 1075 + k + sh, o) | signA) : 0ull;
+  const unsigned long long sb = smag ? (pack_bits(smag, eB - 1075, o) | (sneg ? signA ^ ~kAbs : signA)) : 0ull;
+  const bool trivial = xb == 0ull || d > 54;  // r = A, s = B (B may be zero)
+  ovf |= o && !trivial;
+  TwoSumOut out;
+  out.r = __longlong_as_double((long long)(trivial ? A : rb));
+  out.s = __longlong_as_double((long long)(trivial ? (xb ? B : 0ull) : sb));
+  out.ovf = ovf;
+  return out;
+}
+
+static __device__ __noinline__ TwoSumOut two_sum_int_general(double a, double b) {
+  return two_sum_int_general_body(a, b);
+}
+
+// 64-bit integer arithmetic on 32-bit halves.  Written out with 32-bit
+// instructions (add/sub with carry, clamped funnel shifts) so that it stays
+// on the integer pipe.
+__device__ __forceinline__ void add_u64(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, uint32_t& rh, uint32_t& rl) {
+  asm("add.cc.u32 %1, %3, %5;\n\taddc.u32 %0, %2, %4;" : "=r"(rh), "=r"(rl) : "r"(ah), "r"(al), "r"(bh), "r"(bl));
+}
+__device__ __forceinline__ void sub_u64(uint32_t ah, uint32_t al, uint32_t bh, uint32_t bl, uint32_t& rh, uint32_t& rl) {
+  asm("sub.cc.u32 %1, %3, %5;\n\tsubc.u32 %0, %2, %4;" : "=r"(rh), "=r"(rl) : "r"(ah), "r"(al), "r"(bh), "r"(bl));
+}
+// (hi:lo) <<= n for n in [0, 63]: two clamped funnel-shift stages of at most 32
+__device__ __forceinline__ void shl_u64(uint32_t& hi, uint32_t& lo, uint32_t n) {
+  const uint32_t h1 = __funnelshift_lc(lo, hi, n), l1 = __funnelshift_lc(0u, lo, n);
+  const uint32_t n2 = n > 32u ? n - 32u : 0u;
+  hi = __funnelshift_lc(l1, h1, n2);
+  lo = __funnelshift_lc(0u, l1, n2);
+}
+
+// Alg. 1 split between the pipes, for finite a and b: r = RN(a + b) is one
+// FP64 addition; s = a + b - r is computed exactly on the integer pipe (GB300
+// issues about 60 integer instructions in the time of one FP64 one).  With
+// |A| >= |B| the operands ordered by magnitude, s = B - (r - A) (Fast2Sum,
+// both subtractions exact):
+//   * a zero operand, or a sum that cancels below half of A (|r| < |A|/2:
+//     then a + b is exact), or a subnormal r (likewise exact): s = 0;
+//   * B more than 54 exponent fields below A (B under a quarter ulp of A):
+//     r = A, s = B;
+//   * otherwise, with B's field >= 54 (so s is normal), in units of half of
+//     B's last bit: r - A = |r| - |A| (same sign, r within a factor two of
+//     A) is formed from the significands in units of half of A's last bit,
+//     shifted up by the field difference d <= 54, and subtracted from (or,
+//     for operands of opposite signs, added to) 2 m_B; the result has at
+//     most 53 significant bits and is normalised into s's bits (the hidden
+//     bit carries into the exponent field).  Everything fits 64 bits, held
+//     as 32-bit halves.
+// Other operands (B with field < 54) take two_sum_int_general out of line.
+// ovf is set if r overflows (the FP64 formulas give a non-finite pair).
+// The pair equals the FP64 algorithm's (zero terms may differ in sign,
+// which changes no sum).
+__device__ __forceinline__ void two_sum_split(double a, double b, double& r, double& s, bool& ovf) {
+  r = __dadd_rn(a, b);
+  const uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  const uint32_t bh = (uint32_t)__double2hiint(b), bl = (uint32_t)__double2loint(b);
+  const uint32_t rh = (uint32_t)__double2hiint(r), rl = (uint32_t)__double2loint(r);
+  const uint32_t xah = ah & 0x7FFFFFFFu, xbh = bh & 0x7FFFFFFFu;
+  const bool sw = (xbh > xah) || (xbh == xah && bl > al);
+  const uint32_t Ah = sw ? bh : ah, Al = sw ? bl : al, Bh = sw ? ah : bh, Bl = sw ? al : bl;
+  const uint32_t EA = (Ah >> 20) & 0x7FFu, EB = (Bh >> 20) & 0x7FFu, ER = (rh >> 20) & 0x7FFu;
+  const uint32_t d = EA - EB;
+  if (ER == 0x7FFu) {
+    ovf = true;
+    s = 0.0;
+    return;
+  }
+  if (((Bh & 0x7FFFFFFFu) | Bl) == 0u || ER + 1u < EA || ER == 0u) {
+    s = 0.0;
+    return;
+  }
+  if (d > 54u && EB != 0u) {
+    s = __hiloint2double((int)Bh, (int)Bl);
+    return;
+  }
+  if (EB >= 54u && d <= 54u) {
+    // z = (m_r << (ER + 1 - EA)) - (m_A << 1): |r| - |A| in units of half A's last bit
+    uint32_t zh = (rh & 0xFFFFFu) | 0x100000u, zl = rl;
+    const uint32_t k1 = ER + 1u - EA;  // 0 .. 2
+    zh = __funnelshift_lc(zl, zh, k1);
+    zl = __funnelshift_lc(0u, zl, k1);
+    const uint32_t mah = (Ah & 0xFFFFFu) | 0x100000u;
+    uint32_t th, tl;
+    add_u64(mah, Al, mah, Al, th, tl);
+    sub_u64(zh, zl, th, tl, zh, zl);
+    shl_u64(zh, zl, d);  // r - A in units of half B's last bit (two's complement)
+    const uint32_t mbh = (Bh & 0xFFFFFu) | 0x100000u;
+    uint32_t b2h, b2l;
+    add_u64(mbh, Bl, mbh, Bl, b2h, b2l);  // 2 m_B
+    // s / sign(A) = 2 m_B - z (same signs) or -(2 m_B + z) (opposite signs)
+    const bool opp = (int32_t)(Ah ^ Bh) < 0;
+    uint32_t vh, vl, wh, wl;
+    add_u64(b2h, b2l, zh, zl, wh, wl);
+    sub_u64(b2h, b2l, zh, zl, vh, vl);
+    vh = opp ? wh : vh;
+    vl = opp ? wl : vl;
+    const uint32_t m = (uint32_t)((int32_t)vh >> 31);
+    uint32_t mh, ml;
+    sub_u64(vh ^ m, vl ^ m, m, m, mh, ml);  // |v|
+    const uint32_t sneg = ((m != 0u) != opp) ? 0x80000000u : 0u;
+    const uint32_t c = mh ? (uint32_t)__clz((int)mh) : 32u + (uint32_t)__clz((int)ml);  // 9 .. 64
+    shl_u64(mh, ml, c - 9u);  // leading bit to bit 54 (c = 64 only for |v| = 0)
+    ml = __funnelshift_rc(ml, mh, 2u);
+    mh >>= 2;
+    const uint32_t e = EB + 9u - c;  // exponent field of s minus one
+    const uint32_t sh = (mh + (e << 20)) | ((Ah & 0x80000000u) ^ sneg);
+    s = (mh | ml) ? __hiloint2double((int)sh, (int)ml) : 0.0;
+    return;
+  }
+  const TwoSumOut o = two_sum_int_general(a, b);
+  s = o.s;
+  ovf |= o.ovf;
+}
+
 // Alg. 2
 __device__ __forceinline__ void two_prod(double a, double b, double& r, double& s) {
   r = __dmul_rn(a, b);
@@ -465,16 +651,23 @@ __device__ __forceinline__ bool is_finite_bits(double x) {
   return (((unsigned long long)__double_as_longlong(x) >> 52) & 0x7ffull) != 0x7ffull;
 }
 
+// One level of a cascade: twosum of term i with the carry x (two_sum_split:
+// one FP64 addition, the error on the integer pipe).
+__device__ __forceinline__ void fpe_level(double& fi, double& x, bool& ovf) {
+  double r, s;
+  two_sum_split(fi, x, r, s, ovf);
+  fi = r;
+  x = s;
+}
+
 // Alg. 4 with the early exit of Sec. 4.2; returns the value carried out of
-// the last of the p terms (0 when nothing was lost).
-__device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, double x) {
+// the last of the p terms (0 when nothing was lost).  ovf is set if a term
+// overflows.
+__device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, double x, bool& ovf) {
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) {
     if (i < p) {
-      double r, s;
-      two_sum_ordered(f[i], x, r, s);
-      f[i] = r;
-      x = s;
+      fpe_level(f[i], x, ovf);
       if (is_zero_bits(x)) break;
     }
   }
@@ -485,7 +678,7 @@ __device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, do
 // The loop over b's terms is rolled (the term is picked by selects, so both
 // expansions stay in registers): one copy of Alg. 4's loop instead of
 // kFpeMax keeps the code small.
-__device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[kFpeMax], int p) {
+__device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[kFpeMax], int p, bool& ovf) {
   bool lost = false;
 #pragma unroll 1
   for (int i = 0; i < p; i++) {
@@ -493,24 +686,53 @@ __device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[
 #pragma unroll
     for (int k = 1; k < kFpeMax; k++)
       if (i == k) bi = b[k];
-    if (!is_zero_bits(bi)) lost |= !is_zero_bits(fpe_accumulate(a, p, bi));
+    if (!is_zero_bits(bi)) lost |= !is_zero_bits(fpe_accumulate(a, p, bi, ovf));
   }
   return lost;
 }
 
 constexpr double kTwoProdSafe = 0x1p-969;  // |a*b| >= this: twoprod's error term is exact
 
+// Alg. 4 from term 1 on, for a carry that term 0 has already produced.
+__device__ __forceinline__ double fpe_accumulate_from1(double (&f)[kFpeMax], int p, double x, bool& ovf) {
+#pragma unroll
+  for (int i = 1; i < kFpeMax; i++) {
+    if (i < p) {
+      fpe_level(f[i], x, ovf);
+      if (is_zero_bits(x)) break;
+    }
+  }
+  return x;
+}
+
 // One element of the FPE dot: product into the result expansion, its error
 // into the error expansion.  Returns true if bits may have been lost.
-__device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&err)[kFpeMax], int p, double a, double b) {
+// twoprod (Alg. 2) is two FP64 operations; every twosum of the Accumulate
+// cascades (Alg. 4) is two_sum_split.  The two expansions are independent,
+// so term 0 of both (a level nearly every element reaches) is updated
+// together: two independent dependency chains in flight.  Each expansion
+// still sees exactly Alg. 4's sequence of twosums (twosum(e, 0) = (e, 0),
+// so a zero error term changes nothing).  A product or a term that
+// overflows sets `nonfinite` (the dot's value is then NaN, as the FP64
+// formulas' non-finite terms would make it).
+__device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&err)[kFpeMax], int p, double a, double b,
+                                             bool& nonfinite) {
   if (is_zero_bits(a) || is_zero_bits(b)) return false;  // adds nothing
   double r, s;
   two_prod(a, b, r, s);
   // |r| < 2^-969 (exponent field below 54) or r not finite: bits may be lost
   const unsigned rexp = (unsigned)(((unsigned long long)__double_as_longlong(r) >> 52) & 0x7ffull);
-  bool lost = (rexp < 54u) | (rexp == 0x7ffu);
-  lost |= !is_zero_bits(fpe_accumulate(res, p, r));
-  if (!is_zero_bits(s)) lost |= !is_zero_bits(fpe_accumulate(err, p, s));
+  if (rexp == 0x7ffu) {
+    nonfinite = true;
+    return true;
+  }
+  bool ovf = false;
+  bool lost = rexp < 54u;
+  fpe_level(res[0], r, ovf);
+  fpe_level(err[0], s, ovf);
+  if (!is_zero_bits(r)) lost |= p < 2 || !is_zero_bits(fpe_accumulate_from1(res, p, r, ovf));
+  if (!is_zero_bits(s)) lost |= p < 2 || !is_zero_bits(fpe_accumulate_from1(err, p, s, ovf));
+  nonfinite |= ovf;
   return lost;
 }
 

@@ -10,7 +10,6 @@
 
 #include "device.cuh"
 #include "host.h"
-#include "softeft.cuh"
 
 namespace rpcg {
 
@@ -122,30 +121,36 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
 }
 
 // ------------------------------------------------------------------ FPE dot
-// Elementwise Alg. 1 (which = 0) or Alg. 2 (which = 1) on the integer pipe;
-// zero, non-finite and out-of-range elements take the FP64 formulas, so
-// every output equals the FP64 algorithm's.
+// Alg. 1 in FP64 for the elements two_sum_split does not cover (non-finite
+// operands, sums that overflow).  Out of line, so that the compiler cannot
+// turn this rare path into predicated FP64 work for every element.
+static __device__ __noinline__ double2 eft_twosum_fp64(double x, double y) {
+  double rr, ss;
+  two_sum(x, y, rr, ss);
+  return make_double2(rr, ss);
+}
+
+// Elementwise Alg. 1 (which = 0) as the FPE dot computes it (two_sum_split:
+// one FP64 addition, the error on the integer pipe) or Alg. 2 (which = 1)
+// in FP64 (the FPE dot's twoprod).  Non-finite elements, and sums that
+// overflow, take the FP64 formulas of Alg. 1.
 __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ r,
                       double* __restrict__ s, int which) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double x = a[i], y = b[i];
-    double rr = 0.0, ss = 0.0;
-    bool hw = !isfinite(x) || !isfinite(y) || x == 0.0 || y == 0.0;
-    if (!hw) {
-      SF R, S;
-      bool bad = false;
-      if (which == 0) sf_twosum(sf_from(x), sf_from(y), R, S, bad);
-      else sf_twoprod(x, y, R, S, bad);
-      if (!bad) {
-        rr = sf_to_double(R);
-        ss = sf_to_double(S);
-      } else {
-        hw = true;
+    double rr, ss;
+    if (which == 1) {
+      two_prod(x, y, rr, ss);
+    } else {
+      bool ovf = !is_finite_bits(x) || !is_finite_bits(y);
+      if (!ovf) {
+        two_sum_split(x, y, rr, ss, ovf);
       }
-    }
-    if (hw) {
-      if (which == 0) two_sum(x, y, rr, ss);
-      else two_prod(x, y, rr, ss);
+      if (ovf) {
+        const double2 t = eft_twosum_fp64(x, y);
+        rr = t.x;
+        ss = t.y;
+      }
     }
     r[i] = rr;
     s[i] = ss;
@@ -157,12 +162,13 @@ __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __r
 // (Alg. 3); the threads' expansions then meet exactly in the long
 // accumulator and are rounded once, so the merge loses nothing and *exact
 // reports whether any thread's expansion lost bits (or a product fell below
-// twoprod's exact range).  The element steps of 3 warps in 8 run on the
-// integer pipes (fpe_dot_step_int, the same expansions), the others on the
-// FP64 pipe; capped at 64 registers, 32 warps per SM keep both busy
-// (2^26 pairs: 3.80 ms with every step in FP64 at 16 warps per SM, 2.61 ms).
+// twoprod's exact range).  twoprod takes two FP64 operations per element;
+// each twosum of the Accumulate cascades one FP64 addition, its error being
+// computed on the integer pipe (two_sum_split), where GB300 issues ~60
+// instructions for each FP64 one.
+constexpr int kFpeDotWarps = 32;  // 64 registers (24 and 16 warps per SM measured slower)
 template <int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 4) k_dot_fpe(int64_t n, const double* __restrict__ a,
+__global__ void __launch_bounds__(BLOCK, kFpeDotWarps * 32 / BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,
                                                       const double* __restrict__ b, int p, DotScratch* ws, double* out,
                                                       int32_t* exact) {
   __shared__ unsigned long long sacc[kNDig * kCopies];
@@ -173,18 +179,17 @@ __global__ void __launch_bounds__(BLOCK, 4) k_dot_fpe(int64_t n, const double* _
 #pragma unroll
   for (int i = 0; i < kFpeMax; i++) res[i] = err[i] = 0.0;
   bool lost = false, nonfinite = false;
-  const bool int_warp = fpe_int_warp();
   const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * BLOCK;
-  // compute-bound (the FP64 pipe, and the integer pipes in the warps that
-  // emulate it): no loads run ahead, which keeps registers for more warps
+  // compute-bound: no loads run ahead, which keeps registers for more warps
   for (int64_t i = tid; i < n; i += nthr) {
     const double x = __ldcs(a + i), y = __ldcs(b + i);
     if (!is_finite_bits(x) || !is_finite_bits(y)) nonfinite = true;
-    else if (int_warp) lost |= fpe_dot_step_int(res, err, p, x, y, nonfinite);
-    else lost |= fpe_dot_step(res, err, p, x, y);
+    else lost |= fpe_dot_step(res, err, p, x, y, nonfinite);
   }
-  lost |= fpe_sum(res, err, p);
+  bool ovf = false;
+  lost |= fpe_sum(res, err, p, ovf);
+  nonfinite |= ovf;
   Window win;
   window_init(win);
   const int copy = threadIdx.x & (kCopies - 1);
@@ -311,7 +316,7 @@ static rpcg_status dot_common(int kind, int64_t n, const double* a, const double
     if (kind == 0) {
       launch_dot_exact(n, a, b, ws, out, s);
     } else if (kind == 1) {
-      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kDotMaxGrid, 4), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
+      k_dot_fpe<kDotBlock><<<dot_grid(n, 16, kDotMaxGrid, kFpeDotWarps * 32 / kDotBlock), kDotBlock, 0, s>>>(n, a, b, p, ws, out, exact);
     } else {
       k_dot_plain<kDotBlock><<<dot_grid(n, 4, kDotMaxGrid), kDotBlock, 0, s>>>(n, a, b, ws, out);
     }

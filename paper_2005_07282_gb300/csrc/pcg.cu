@@ -26,7 +26,6 @@
 
 #include "device.cuh"
 #include "host.h"
-#include "softeft.cuh"
 #include "solver.cuh"
 
 namespace rpcg {
@@ -97,10 +96,9 @@ __device__ __forceinline__ FinalScratch* red_carve(unsigned char* base, unsigned
   return fs;
 }
 
-// kIntShare (fpe): a share of the warps run the element steps on the
-// integer pipes (fpe_int_warp): in kernels capped at 64 registers for 32
-// warps per SM, where both kinds of pipe then stay busy.
-template <int V, int NACC, bool kIntShare = false>
+// fpe: twoprod in FP64, the Accumulate cascades with two_sum_split (one FP64
+// addition per twosum, the error on the integer pipe).
+template <int V, int NACC>
 __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long* sacc, int j, double a, double b,
                                         int p) {
   if constexpr (V == RPCG_EXBLAS) {
@@ -109,8 +107,7 @@ __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long*
     exact_deposit(R.win[j], sacc + j * kNDig * kCopies, threadIdx.x & (kCopies - 1), e);
   } else if constexpr (V == RPCG_FPE) {
     if (!is_finite_bits(a) || !is_finite_bits(b)) R.bad = true;
-    else if (kIntShare && fpe_int_warp()) R.lost[j] |= fpe_dot_step_int(R.res[j], R.err[j], p, a, b, R.bad);
-    else R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b);
+    else R.lost[j] |= fpe_dot_step(R.res[j], R.err[j], p, a, b, R.bad);
   } else {
     R.acc[j] = __fma_rn(a, b, R.acc[j]);
   }
@@ -138,7 +135,7 @@ __device__ bool red_finish(Reducer<V, NACC>& R, unsigned long long* sacc, PassSc
     bool bad = R.bad;
 #pragma unroll  // constant indices keep the expansions in registers
     for (int j = 0; j < NACC; j++) {
-      R.lost[j] |= fpe_sum(R.res[j], R.err[j], p);
+      R.lost[j] |= fpe_sum(R.res[j], R.err[j], p, bad);
       if (R.lost[j]) atomicOr(&ws->flags, 2u << j);
       window_init(R.win[j]);
 #pragma unroll
@@ -319,13 +316,10 @@ __global__ void __launch_bounds__(BLOCK) k_spmv(MatDev m, const double* __restri
   for (int row = blockIdx.x * BLOCK + threadIdx.x; row < m.n; row += gridDim.x * BLOCK) y[row] = sell_row(m, row, x);
 }
 
-// Pass A: S1 + S2.  The fpe variant's pass A (SpMV and one FPE dot) is
-// capped at 64 registers with a share of its warps on the integer pipes:
-// 291 iterations/s on the 27-point 256^3 system, 259 without the cap.  The
-// other variants keep the compiler's own register choice (minimum blocks 0:
-// an explicit 1 let the exact pass A grow to 110 registers and fall from
-// 1.01 to 1.51 ms at 256^3).
-constexpr bool kPassAIntShare = true;
+// Pass A: S1 + S2 (the fpe variant uses k_spmv + k_pass_a_dot instead).
+// The compiler keeps its own register choice (minimum blocks 0: an explicit
+// 1 let the exact pass A grow to 110 registers and fall from 1.01 to 1.51 ms
+// at 256^3); the fpe instance is capped at 64 registers (32 warps per SM).
 template <int V, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 0)
     k_pass_a(MatDev m, const double* __restrict__ d, double* __restrict__ w, PassScratch* ws, SolveState* st,
@@ -345,7 +339,7 @@ __global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 0)
   for (int row = blockIdx.x * BLOCK + threadIdx.x; row < m.n; row += gridDim.x * BLOCK) {
     const double v = sell_row(m, row, d);
     w[row] = v;
-    red_add<V, 1, kPassAIntShare>(R, sacc, 0, __ldg(d + row), v, p);
+    red_add<V, 1>(R, sacc, 0, __ldg(d + row), v, p);
   }
   if (red_finish<V, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     if (st->status != 0) {
@@ -353,6 +347,47 @@ __global__ void __launch_bounds__(BLOCK, V == RPCG_FPE ? 1024 / BLOCK : 0)
       return;
     }
     if (V == RPCG_FPE && fs->lost[0]) {
+      st->fpe_inexact += 1;
+      fpe_grow(st, args);
+      if (!args->fpe_strict) {
+        st->redo = 1;  // recompute this dot exactly (k_redo_a)
+        return;
+      }
+    }
+    finalize_a(fs->value[0], st, args, cond);
+  }
+}
+
+// FPE variant, pass A as two kernels: k_spmv writes w = A d (S1), then
+// this kernel streams d and w (16 bytes a row more than a fused pass) and
+// forms the FPE dot <d, w> (S2) with the finalisation of k_pass_a.  Each
+// kernel fits 64 registers without spilling (the fused pass spilled ~0.8 KB
+// per thread at that cap; both forms measured 1.55 ms per pass at 256^3).
+template <int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_a_dot(int n, const double* __restrict__ d,
+                                                                    const double* __restrict__ w, PassScratch* ws,
+                                                                    SolveState* st, const SolveArgs* args,
+                                                                    cudaGraphConditionalHandle cond) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  unsigned long long* sacc;
+  FinalScratch* fs = red_carve<RPCG_FPE, 1>(smem, sacc);
+  if (st->status != 0) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) stop_loop(st, args, cond);
+    return;
+  }
+  const int p = st->fpe_p;
+  smem_acc_zero(sacc);
+  __syncthreads();
+  Reducer<RPCG_FPE, 1> R;
+  red_init(R);
+  for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK)
+    red_add<RPCG_FPE, 1>(R, sacc, 0, __ldcs(d + i), __ldcs(w + i), p);
+  if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
+    if (st->status != 0) {
+      stop_loop(st, args, cond);
+      return;
+    }
+    if (fs->lost[0]) {
       st->fpe_inexact += 1;
       fpe_grow(st, args);
       if (!args->fpe_strict) {
@@ -439,9 +474,7 @@ __global__ void __launch_bounds__(BLOCK) k_pass_b(int n, const double* __restric
 }
 
 // FPE variant: pass B as two kernels, so that each thread holds one pair of
-// expansions instead of two.  With that, 64 registers (32 warps per SM)
-// suffice and a share of the warps can run their element steps on the
-// integer pipes (fpe_int_warp), while the rest use the FP64 pipe.  B1: S3,
+// expansions instead of two and 64 registers (32 warps per SM) suffice.  B1: S3,
 // S4, S5 and S6 (<z,r>, kept in the state); B2: S8 (<r,r> of the new r)
 // and the finalisation of both dots, with the counting and recompute rules
 // of pass B.
@@ -471,7 +504,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_b1(int n, const do
     const double zi = __dmul_rn(__ldcs(inv + i), ri);
     __stcs(x + i, xi);
     r[i] = ri;  // read again by B2
-    red_add<RPCG_FPE, 1, true>(R, sacc, 0, zi, ri, p);
+    red_add<RPCG_FPE, 1>(R, sacc, 0, zi, ri, p);
   }
   if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     st->zr = fs->value[0];
@@ -494,7 +527,7 @@ __global__ void __launch_bounds__(BLOCK, 1024 / BLOCK) k_pass_b2(int n, const do
   red_init(R);
   for (int i = blockIdx.x * BLOCK + threadIdx.x; i < n; i += gridDim.x * BLOCK) {
     const double ri = __ldcs(r + i);
-    red_add<RPCG_FPE, 1, true>(R, sacc, 0, ri, ri, p);
+    red_add<RPCG_FPE, 1>(R, sacc, 0, ri, ri, p);
   }
   if (red_finish<RPCG_FPE, 1, BLOCK>(R, sacc, ws, fs, p) && threadIdx.x == 0) {
     const bool lost0 = st->zr_lost != 0, lost1 = fs->lost[0] != 0;
@@ -716,6 +749,7 @@ static rpcg_status launch_cfg(int n, int grid, LaunchCfg* c) {
   RPCG_CUDA_TRY(set_smem(k_spmv<BLOCK>, c->smem_spmv));
   RPCG_CUDA_TRY(set_smem(k_pass_a<V, BLOCK>, c->smem_a));
   if constexpr (V == RPCG_FPE) {
+    RPCG_CUDA_TRY(set_smem(k_pass_a_dot<BLOCK>, c->smem_a));
     RPCG_CUDA_TRY(set_smem(k_pass_b1<BLOCK>, c->smem_a));  // one FPE dot each, as pass A
     RPCG_CUDA_TRY(set_smem(k_pass_b2<BLOCK>, c->smem_a));
   } else {
@@ -777,7 +811,13 @@ static rpcg_status build_graph(rpcg_matrix_t A, int grid, cudaGraph_t* out_graph
   RPCG_CUDA_TRY(cudaGraphAddNode(&n_loop, g, &n_setup, nullptr, 1, &cp));
   cudaGraph_t body = cp.conditional.phGraph_out[0];
   cudaGraphNode_t b_a, b_ra, b_b, b_rb, b_c;
-  {
+  if (V == RPCG_FPE) {
+    cudaGraphNode_t b_s;
+    void* as[] = {&m, &d, &w};
+    RPCG_CUDA_TRY(add_kernel(body, &b_s, nullptr, 0, (const void*)k_spmv<BLOCK>, grid_tiles, BLOCK, smem_spmv, as));
+    void* a[] = {&n, &d, &w, &ws, &st, &args, &cond};
+    RPCG_CUDA_TRY(add_kernel(body, &b_a, &b_s, 1, (const void*)k_pass_a_dot<BLOCK>, grid_stream, BLOCK, smem_a, a));
+  } else {
     void* a[] = {&m, &d, &w, &ws, &st, &args, &cond};
     RPCG_CUDA_TRY(add_kernel(body, &b_a, nullptr, 0, (const void*)k_pass_a<V, BLOCK>, grid_tiles, BLOCK, smem_a, a));
   }
@@ -889,7 +929,12 @@ static rpcg_status run_eager(rpcg_matrix_t A, int grid, const double* x0, cudaSt
   cnt[0] += 1;
   while (A->h_state->active) {
     cudaEventRecord(ev[2], s);
-    k_pass_a<V, BLOCK><<<c.grid_tiles, BLOCK, c.smem_a, s>>>(m, d, w, ws, st, args, cond);
+    if (V == RPCG_FPE) {
+      k_spmv<BLOCK><<<c.grid_tiles, BLOCK, c.smem_spmv, s>>>(m, d, w);
+      k_pass_a_dot<BLOCK><<<c.grid_stream, BLOCK, c.smem_a, s>>>(n, d, w, ws, st, args, cond);
+    } else {
+      k_pass_a<V, BLOCK><<<c.grid_tiles, BLOCK, c.smem_a, s>>>(m, d, w, ws, st, args, cond);
+    }
     cudaEventRecord(ev[3], s);
     if (V == RPCG_FPE) k_redo_a<BLOCK><<<c.grid_stream, BLOCK, c.smem_ra, s>>>(n, d, w, ws, st, args, cond);
     cudaEventRecord(ev[4], s);

@@ -143,10 +143,10 @@ def _one_thread(vals_a, vals_b, t, n=2048, nthr=256):
 
 @pytest.mark.parametrize("p", [1, 2, 8])
 def test_dot_fpe_integer_and_fp64_warps_agree(rpcg, cuda, oracle_lib, p):
-    """A share of the FPE dot's warps runs the element steps on the integer
-    pipes, the rest in FP64.  A thread's expansion depends only on its own
-    products, so the same products placed in a thread of either kind of warp
-    give the same value and flag, bit for bit: lossy ill-conditioned sums,
+    """A thread's expansions depend only on its own products, so the same
+    products placed in any thread (of any warp, whichever pipe runs its
+    Accumulate cascades) give the same value and flag, bit for bit, and the
+    paper's one-thread FPE dot gives them too: lossy ill-conditioned sums,
     products below twoprod's exact range, subnormal products, sums that
     overflow, cancellation to zero."""
     rng = np.random.default_rng(5)
@@ -159,7 +159,7 @@ def test_dot_fpe_integer_and_fp64_warps_agree(rpcg, cuda, oracle_lib, p):
         ([1.0, -1.0, 2.0 ** 60, -(2.0 ** 60), 3.0, -3.0, 0.5, -0.5], [1.0] * 8),  # cancels to +0
         ([2.0 ** -1074, 3.0, 2.0 ** -1000, 1.0, 1.0, 1.0, 1.0, 1.0], [1.0, 2.0 ** -1074, 2.0 ** -30, 1e-16, 1.0, -1e-16, 3.0, 2.0 ** 52]),
     ]
-    # threads 0, 40 and 95 are in warps 0-2 (integer pipes); 96, 160 and 255 in FP64 warps
+    # threads in the first and last warps of the CTA and in between
     for va, vb in cases:
         got = []
         for t in (0, 40, 95, 96, 160, 255):

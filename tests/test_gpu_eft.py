@@ -1,6 +1,7 @@
-"""The error-free transformations computed on the integer pipe (the FPE
-dot's arithmetic) against the oracle's FP64 Alg. 1 and Alg. 2, element by
-element, on random and adversarial inputs."""
+"""The FPE dot's error-free transformations -- twosum (Alg. 1) as exact
+integer arithmetic on the bit patterns, twoprod (Alg. 2) in FP64 -- against
+the oracle's FP64 Alg. 1 and Alg. 2, element by element, on random and
+adversarial inputs."""
 import math
 import random
 
@@ -66,8 +67,9 @@ def test_twoprod_matches_oracle(rpcg, cuda, oracle_lib, seed):
 
 
 def test_fpe_dot_integer_pipe_matches_fp64_semantics(rpcg, cuda, oracle_lib):
-    """The FPE dot on the integer pipe equals the exact dot whenever its
-    flag holds, on small ill-conditioned cases and every expansion size."""
+    """The FPE dot (its Accumulate cascades on the integer pipe) equals the
+    exact dot whenever its flag holds, on small ill-conditioned cases and
+    every expansion size."""
     import torch
     for fam_c in (1e8, 1e24, 1e40):
         a, b = synth.dot_family_c(64, fam_c, 5)

@@ -6,7 +6,7 @@ import pytest
 import scipy.sparse
 
 import synth
-from conftest import bits
+from conftest import bits, pcg_2x2_golden
 
 pytestmark = pytest.mark.gpu
 
@@ -218,3 +218,23 @@ def test_cluster_size_boundary(rpcg, cuda, oracle_lib, n):
     assert rc["iterations"] == rg["iterations"] == ref["iterations"]
     assert np.array_equal(bits(xc), bits(ref["x"])) and np.array_equal(bits(xg), bits(ref["x"]))
     assert np.array_equal(bits(hc), bits(ref["history"]))
+
+
+@pytest.mark.parametrize("variant", ["exblas", "fpe"])
+@pytest.mark.parametrize("path", ["cluster", "graph"])
+def test_2x2_hand_worked_trace(rpcg, cuda, variant, path):
+    """The CUDA solve of the 2x2 system of tests/golden/pcg_2x2_trace.txt
+    after one and after two loop bodies: x, tau and every relres equal the
+    trace worked out by hand (exact rational arithmetic, one rounding per
+    operation with the fma forms of Sec. 4.3), on both paths."""
+    A, b, want = pcg_2x2_golden()
+    M = rpcg.Matrix.from_csr(A)
+    kw = {} if path == "cluster" else dict(block=128, grid=1)
+    assert M.solve_path(variant, **kw) == path
+    for its in (1, 2):
+        r, x, h = _solve(M, b, cuda, variant, tol=0.0, max_iter=its, **kw)
+        assert r["status"] == rpcg.NOT_CONVERGED and r["iterations"] == its
+        assert np.array_equal(bits(x), bits(want[its]["x"]))
+        assert bits([r["tau"]])[0] == bits(want[its]["tau"])[0]
+        assert np.array_equal(bits(h), bits([want[l]["relres"][0] for l in range(its + 1)]))
+    M.close()
