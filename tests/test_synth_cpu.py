@@ -74,3 +74,15 @@ def test_diffusion_batch_sizes():
     for A, b in zip(mats, rhs):
         s = round(A.n ** (1 / 3))
         assert s ** 3 == A.n and 8 <= s <= 64 and b.shape == (A.n,)
+
+
+def test_family_c_realised_condition_number(oracle_lib):
+    """The ill-conditioned family's realised condition number
+    2 sum|a_i b_i| / |a . b| (denominator from the oracle's exact dot) stays
+    within a small factor of the requested one, at small and large n."""
+    import numpy as np
+    for cond in (1e8, 1e16, 1e24, 1e32, 1e40):
+        for n in (4096, 1 << 18):
+            a, b = synth.dot_family_c(n, cond, synth.BASE_SEED + 1)
+            realised = 2.0 * float(np.sum(np.abs(a) * np.abs(b))) / abs(oracle_lib.dot_exact(a, b))
+            assert cond / 10 <= realised <= cond * 30, (cond, n, realised)
