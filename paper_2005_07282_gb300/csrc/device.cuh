@@ -644,6 +644,55 @@ __device__ __forceinline__ void two_prod(double a, double b, double& r, double& 
   s = __fma_rn(a, b, -r);
 }
 
+// Alg. 2 on the integer pipe for two normal operands whose product has an
+// exponent field in [107, 2045] (|a b| from 2^-916 up, no overflow; s is
+// then normal or zero); returns false for other operands, which take
+// two_prod (FP64 multiply and fma use four FP64-pipe slots on GB300, a
+// half-rate pipe).  The 106-bit product of the significands comes from
+// four 32x32-bit multiplies; r keeps its top 53 bits rounded to nearest
+// even (the bits below are the sticky part), and s = the dropped bits minus
+// the rounding increment, normalised.  The same pair as Alg. 2 (checked
+// elementwise against the FP64 formulas).
+__device__ __forceinline__ bool two_prod_int(double a, double b, double& r, double& s) {
+  const uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  const uint32_t bh = (uint32_t)__double2hiint(b), bl = (uint32_t)__double2loint(b);
+  const uint32_t EA = (ah >> 20) & 0x7FFu, EB = (bh >> 20) & 0x7FFu;
+  const int fr = (int)(EA + EB) - 1023;  // r's exponent field if the product has 105 bits (106: one more)
+  if (EA == 0u || EB == 0u || EA == 0x7FFu || EB == 0x7FFu || fr < 107 || fr > 2045) return false;
+  const uint32_t mah = (ah & 0xFFFFFu) | 0x100000u, mbh = (bh & 0xFFFFFu) | 0x100000u;
+  // product (w3:w2:w1:w0) = (mah:al) (mbh:bl)
+  const uint64_t p0 = (uint64_t)al * bl, p2 = (uint64_t)mah * mbh;
+  const uint64_t p1 = (uint64_t)al * mbh + (uint64_t)mah * bl;  // < 2^54
+  const uint32_t w0 = (uint32_t)p0;
+  uint32_t w1, w2, w3;
+  asm("add.cc.u32 %0, %3, %4;\n\t"
+      "addc.cc.u32 %1, %5, %6;\n\t"
+      "addc.u32 %2, %7, 0;"
+      : "=r"(w1), "=r"(w2), "=r"(w3)
+      : "r"((uint32_t)(p0 >> 32)), "r"((uint32_t)p1), "r"((uint32_t)(p1 >> 32)), "r"((uint32_t)p2),
+        "r"((uint32_t)(p2 >> 32)));
+  const uint32_t big = w3 >> 9;     // the product has 106 bits (top bit 105) or 105
+  const uint32_t sh32 = 20u + big;  // bits dropped: 52 + big = 32 + sh32
+  const uint32_t qh = __funnelshift_rc(w2, w3, sh32), ql = __funnelshift_rc(w1, w2, sh32);
+  const uint32_t lowh = w1 & ((1u << sh32) - 1u), halfh = 1u << (sh32 - 1u);  // dropped bits (lowh:w0), half = halfh:0
+  const bool up = lowh > halfh || (lowh == halfh && (w0 != 0u || (ql & 1u)));
+  uint32_t rqh, rql;
+  add_u64(qh, ql, 0u, up ? 1u : 0u, rqh, rql);
+  const uint32_t sign = (ah ^ bh) & 0x80000000u;
+  r = __hiloint2double((int)((rqh + ((uint32_t)(fr - 1 + (int)big) << 20)) | sign), (int)rql);
+  // s = dropped bits - up 2^(52 + big), in units of the product's last bit
+  uint32_t vh = lowh, vl = w0;
+  if (up) sub_u64(lowh, w0, 1u << sh32, 0u, vh, vl);
+  const uint32_t m = (uint32_t)((int32_t)vh >> 31);
+  uint32_t mh, ml;
+  sub_u64(vh ^ m, vl ^ m, m, m, mh, ml);
+  const uint32_t c = mh ? (uint32_t)__clz((int)mh) : 32u + (uint32_t)__clz((int)ml);  // 11 .. 64
+  shl_u64(mh, ml, c - 11u);  // leading bit to bit 52
+  const uint32_t sb = (mh + ((EA + EB - 1065u - c) << 20)) | (sign ^ (m ? 0x80000000u : 0u));
+  s = (mh | ml) ? __hiloint2double((int)sb, (int)ml) : 0.0;
+  return true;
+}
+
 // Tests on the bit pattern (integer pipe), keeping the scarce FP64 pipe for
 // the arithmetic of the error-free transformations.
 __device__ __forceinline__ bool is_zero_bits(double x) { return ((unsigned long long)__double_as_longlong(x) << 1) == 0ull; }
@@ -707,8 +756,8 @@ __device__ __forceinline__ double fpe_accumulate_from1(double (&f)[kFpeMax], int
 
 // One element of the FPE dot: product into the result expansion, its error
 // into the error expansion.  Returns true if bits may have been lost.
-// twoprod (Alg. 2) is two FP64 operations; every twosum of the Accumulate
-// cascades (Alg. 4) is two_sum_split.  The two expansions are independent,
+// twoprod (Alg. 2) is two_prod_int (FP64 only for out-of-range operands);
+// every twosum of the Accumulate cascades (Alg. 4) is two_sum_split.  The two expansions are independent,
 // so term 0 of both (a level nearly every element reaches) is updated
 // together: two independent dependency chains in flight.  Each expansion
 // still sees exactly Alg. 4's sequence of twosums (twosum(e, 0) = (e, 0),
@@ -719,7 +768,7 @@ __device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&er
                                              bool& nonfinite) {
   if (is_zero_bits(a) || is_zero_bits(b)) return false;  // adds nothing
   double r, s;
-  two_prod(a, b, r, s);
+  if (!two_prod_int(a, b, r, s)) two_prod(a, b, r, s);
   // |r| < 2^-969 (exponent field below 54) or r not finite: bits may be lost
   const unsigned rexp = (unsigned)(((unsigned long long)__double_as_longlong(r) >> 52) & 0x7ffull);
   if (rexp == 0x7ffu) {

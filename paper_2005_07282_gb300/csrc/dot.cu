@@ -130,17 +130,17 @@ static __device__ __noinline__ double2 eft_twosum_fp64(double x, double y) {
   return make_double2(rr, ss);
 }
 
-// Elementwise Alg. 1 (which = 0) as the FPE dot computes it (two_sum_split:
-// one FP64 addition, the error on the integer pipe) or Alg. 2 (which = 1)
-// in FP64 (the FPE dot's twoprod).  Non-finite elements, and sums that
-// overflow, take the FP64 formulas of Alg. 1.
+// Elementwise Alg. 1 (which = 0) or Alg. 2 (which = 1) as the FPE dot
+// computes them: two_sum_split (one FP64 addition, the error on the integer
+// pipe; non-finite elements and sums that overflow take the FP64 formulas)
+// and two_prod_int (the FP64 formulas outside its range).
 __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __restrict__ b, double* __restrict__ r,
                       double* __restrict__ s, int which) {
   for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
     const double x = a[i], y = b[i];
     double rr, ss;
     if (which == 1) {
-      two_prod(x, y, rr, ss);
+      if (!two_prod_int(x, y, rr, ss)) two_prod(x, y, rr, ss);
     } else {
       bool ovf = !is_finite_bits(x) || !is_finite_bits(y);
       if (!ovf) {
@@ -162,10 +162,10 @@ __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __r
 // (Alg. 3); the threads' expansions then meet exactly in the long
 // accumulator and are rounded once, so the merge loses nothing and *exact
 // reports whether any thread's expansion lost bits (or a product fell below
-// twoprod's exact range).  twoprod takes two FP64 operations per element;
-// each twosum of the Accumulate cascades one FP64 addition, its error being
-// computed on the integer pipe (two_sum_split), where GB300 issues ~60
-// instructions for each FP64 one.
+// twoprod's exact range).  twoprod runs on the integer pipe
+// (two_prod_int), each twosum of the Accumulate cascades takes one FP64
+// addition with its error computed on the integer pipe (two_sum_split):
+// GB300's FP64 pipe is half rate.
 constexpr int kFpeDotWarps = 32;  // 64 registers (24 and 16 warps per SM measured slower)
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kFpeDotWarps * 32 / BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,

@@ -62,8 +62,15 @@ __device__ __forceinline__ long long sell_index(const MatDev& m, int row, int k)
 // slices.  The matrix stream is read with coalesced streaming loads; the
 // gathers x[col] go through L1/L2 (stencil locality).  The loads of the
 // next 8 entries are issued before the FMAs of the current 8.
-// The row whose entry k sits at base + 32 k, of length len.
-__device__ __forceinline__ double sell_row_at(const MatDev& m, long long base, int len, const double* __restrict__ x) {
+//
+// The loads run over the slice's length (its longest row, from the slice
+// offsets), not the row's own: padding entries hold column 0 and value 0,
+// so every load stays in range, and the loads need not wait for the row
+// pointers.  Only entries k < len (the row's length) enter the fma chain.
+// The row whose entry k sits at base + 32 k, of length len, in a slice of
+// length slen >= len.
+__device__ __forceinline__ double sell_row_at(const MatDev& m, long long base, int len, int slen,
+                                              const double* __restrict__ x) {
   constexpr int U = 8;
   const double* __restrict__ vp = m.val + base;
   const int* __restrict__ cp = m.col + base;
@@ -73,19 +80,19 @@ __device__ __forceinline__ double sell_row_at(const MatDev& m, long long base, i
   for (int j = 0; j < U; j++) {
     xa[j] = 0.0;
     va[j] = 0.0;
-    if (j < len) {
+    if (j < slen) {
       va[j] = __ldcs(vp + 32 * j);
       xa[j] = __ldg(x + __ldcs(cp + 32 * j));
     }
   }
-  for (int k = 0; k < len; k += U) {
+  for (int k = 0; k < slen; k += U) {
     double xb[U], vb[U];
 #pragma unroll
     for (int j = 0; j < U; j++) {
       const int kk = k + U + j;
       xb[j] = 0.0;
       vb[j] = 0.0;
-      if (kk < len) {
+      if (kk < slen) {
         vb[j] = __ldcs(vp + 32ll * kk);
         xb[j] = __ldg(x + __ldcs(cp + 32ll * kk));
       }
@@ -102,27 +109,37 @@ __device__ __forceinline__ double sell_row_at(const MatDev& m, long long base, i
   return acc;
 }
 
-__device__ __forceinline__ double sell_row(const MatDev& m, int row, const double* __restrict__ x) {
-  const int len = __ldg(m.rowptr + row + 1) - __ldg(m.rowptr + row);
-  return sell_row_at(m, sell_index(m, row, 0), len, x);
+// Slice offset of `row`'s slice and that slice's length (entries per row).
+__device__ __forceinline__ long long sell_slice(const MatDev& m, int row, int& slen) {
+  const long long s0 = __ldg(m.sptr + (row >> 5)), s1 = __ldg(m.sptr + (row >> 5) + 1);
+  slen = (int)((s1 - s0) >> 5);
+  return s0;
 }
 
-// Two rows at once (ya = row ra of A x, yb = row rb): when both have at
-// most 8 entries, their loads are issued together, so a thread keeps two
-// rows' memory chains in flight with the registers sell_row spends on
-// prefetching a row's next 8 entries.  Longer rows take sell_row.  Each
-// row's fma chain is the one of sell_row.
+__device__ __forceinline__ double sell_row(const MatDev& m, int row, const double* __restrict__ x) {
+  int slen;
+  const long long s0 = sell_slice(m, row, slen);
+  const int len = __ldg(m.rowptr + row + 1) - __ldg(m.rowptr + row);
+  return sell_row_at(m, s0 + (row & 31), len, slen, x);
+}
+
+// Two rows at once (ya = row ra of A x, yb = row rb): when both slices have
+// at most 8 entries per row, the loads of both rows are issued together, so
+// a thread keeps two rows' memory chains in flight with the registers
+// sell_row spends on prefetching a row's next 8 entries.  Longer rows take
+// sell_row.  Each row's fma chain is the one of sell_row.
 __device__ __forceinline__ void sell_rows2(const MatDev& m, int ra, int rb, const double* __restrict__ x, double& ya,
                                            double& yb) {
   constexpr int U = 8;
-  const int la = __ldg(m.rowptr + ra + 1) - __ldg(m.rowptr + ra);
-  const int lb = __ldg(m.rowptr + rb + 1) - __ldg(m.rowptr + rb);
-  if (la > U || lb > U) {
+  int sa, sb;
+  const long long ba = sell_slice(m, ra, sa) + (ra & 31), bb = sell_slice(m, rb, sb) + (rb & 31);
+  if (sa > U || sb > U) {
     ya = sell_row(m, ra, x);
     yb = sell_row(m, rb, x);
     return;
   }
-  const long long ba = sell_index(m, ra, 0), bb = sell_index(m, rb, 0);
+  const int la = __ldg(m.rowptr + ra + 1) - __ldg(m.rowptr + ra);
+  const int lb = __ldg(m.rowptr + rb + 1) - __ldg(m.rowptr + rb);
   double va[U], xa[U], vb[U], xb[U];
 #pragma unroll
   for (int j = 0; j < U; j++) {
@@ -130,11 +147,11 @@ __device__ __forceinline__ void sell_rows2(const MatDev& m, int ra, int rb, cons
     xa[j] = 0.0;
     vb[j] = 0.0;
     xb[j] = 0.0;
-    if (j < la) {
+    if (j < sa) {
       va[j] = __ldcs(m.val + ba + 32 * j);
       xa[j] = __ldg(x + __ldcs(m.col + ba + 32 * j));
     }
-    if (j < lb) {
+    if (j < sb) {
       vb[j] = __ldcs(m.val + bb + 32 * j);
       xb[j] = __ldg(x + __ldcs(m.col + bb + 32 * j));
     }
