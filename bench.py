@@ -97,7 +97,16 @@ def workload(side, stencil=27, band=0, band_n=0):
 # capture summarised in profiles/k_pass_a_p27_128.md (dram read + write of the
 # 128^3 case / its algorithmic bytes); the kernel streams every matrix entry
 # once, so the full-size launch's traffic is this ratio times its bytes.
-PASS_A_TRAFFIC_RATIO = 701.9 / 710.9
+PASS_A_TRAFFIC_RATIO = 702.0 / 710.9
+
+
+# Pipe utilisation of the fpe variant's three FPE-dot kernels, from the ncu
+# full-set capture summarised in profiles/k_fpe_dots_p27_128.md (27-point
+# 128^3, percent of each pipe's own peak while the SMs are active).  The
+# FP64 pipe, half rate on this GPU, is the busiest unit: the fpe roof.
+FPE_PIPES = {"k_pass_a_dot": {"fp64": 75.1, "alu": 55.3, "issue": 49.2},
+             "k_pass_b1": {"fp64": 75.2, "alu": 46.4, "issue": 43.0},
+             "k_pass_b2": {"fp64": 73.4, "alu": 60.7, "issue": 53.2}}
 
 
 def wl_name(args):
@@ -415,6 +424,12 @@ def gpu_arm(args, rank, world, local_rank):
         pf = M.solve_profiled(d_b, x, variant="fpe", tol=args.tol, max_iter=min(30, iters_per_solve))
         lf = max(pf["launches"]["A"], 1)
         extras["pass_ms_fpe"] = {k: pf["pass_ms"][k] / lf for k in ("A", "B", "C")}
+        fpe_ms = 1e3 / extras["fpe_iters_per_s"]
+        extras["fpe_roofline"] = {
+            "bound": "fp64", "kernels": "k_pass_a_dot, k_pass_b1, k_pass_b2 (the iteration's three FPE dots)",
+            "pipe_active_pct": FPE_PIPES, "source": "ncu --set full, 27-point 128^3 (profiles/k_fpe_dots_p27_128.md)",
+            "iteration_ms": fpe_ms, "iteration_hbm_frac": iter_bytes(n, nnz) / (fpe_ms * 1e-3) / 1e9 / hbm_peak()[0],
+            "overhead_vs_plain": plain_rate / extras["fpe_iters_per_s"]}
         it_ms = ms / max(total_iters, 1)
         extras["iteration_roofline"] = {"bytes_per_iter": iter_bytes(n, nnz), "ms_per_iter": it_ms,
                                         "achieved_gbs": iter_bytes(n, nnz) / (it_ms * 1e-3) / 1e9,
