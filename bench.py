@@ -265,6 +265,13 @@ def cpu_oracle_rate(A, b, iters, tol, nthreads=None):
     return r["iterations"] / max(r["loop_seconds"], 1e-9), r["iterations"], r["loop_seconds"], nt
 
 
+def workload_config(args, n, nnz):
+    """The workload both arms measure (the reference arm's config equals this one)."""
+    return {"workload": wl_name(args) + " " + args.variant, "n": n, "nnz": nnz, "tol": args.tol,
+            "max_iter": args.max_iter, "l2": l2_note(n, nnz), "parallelism": f"replicas x{args.gpus}",
+            "metric_unit": "PCG iterations (loop bodies) per second"}
+
+
 def reference_arm(args, rank, world):
     """--impl reference: the CPU oracle, timed on the host cores (rank 0 only)."""
     if rank != 0:
@@ -285,8 +292,9 @@ def reference_arm(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "iters/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": wl_name(args), "n": A.n, "nnz": A.nnz, "tol": args.tol,
-                       "step": f"{per_step} PCG iterations of the oracle (set-up excluded from the time)"},
+            "config": workload_config(args, A.n, A.nnz),
+            "run": {"step": f"{per_step} PCG iterations of the oracle on the host cores (set-up excluded "
+                            "from the time); the exact-dot trajectory the exblas variant follows"},
             "cpu_baseline": {"value": v, "unit": "iters/s", "cores": nt, "kind": "oracle",
                              "sample": f"{args.steps} x {per_step} iterations of the exact-dot PCG"},
             "e2e": {"value": v, "unit": "iters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -503,14 +511,12 @@ def gpu_arm(args, rank, world, local_rank):
         line = {"metric": METRIC, "value": value, "unit": "iters/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": wl_name(args) + " " + args.variant, "n": n, "nnz": nnz, "tol": args.tol,
-                           "max_iter": args.max_iter, "iterations_per_solve": iters_per_solve,
-                           "solve_status": status, "step": "one complete solve from x0 = 0",
-                           "l2": l2_note(n, nnz),
-                           "parallelism": f"replicas x{world}",
-                           "launch": "eager (kernel by kernel)" if args.eager else
-                           ("one cluster-resident launch per solve" if path == "cluster" else
-                            "CUDA graph, device-side loop")},
+                "config": workload_config(args, n, nnz),
+                "run": {"iterations_per_solve": iters_per_solve, "solve_status": status,
+                        "step": "one complete solve from x0 = 0",
+                        "launch": "eager (kernel by kernel)" if args.eager else
+                        ("one cluster-resident launch per solve" if path == "cluster" else
+                         "CUDA graph, device-side loop")},
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, **extras}
         print(json.dumps(line), flush=True)

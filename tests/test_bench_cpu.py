@@ -44,6 +44,7 @@ def test_reference_arm_json_line():
 
     class A:
         side, stencil, steps, warmup, tol, band, band_n = 6, 7, 1, 1, 1e-8, 0, 0
+        variant, max_iter, gpus = "exblas", 5000, 1
 
     buf = io.StringIO()
     with contextlib.redirect_stdout(buf):
@@ -55,4 +56,6 @@ def test_reference_arm_json_line():
     assert line["impl"] == "reference" and line["unit"] == "iters/s" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] >= 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["e2e"]["d2h_bytes_per_step"] == 0
-    assert line["config"]["workload"] == "poisson7_6"
+    assert line["config"]["workload"] == "poisson7_6 exblas"
+    # the same workload record as the GPU arm's line (the driver compares the two arms)
+    assert line["config"] == bench.workload_config(A, line["config"]["n"], line["config"]["nnz"])
