@@ -71,6 +71,37 @@ def test_dot_exact_extreme_exponents(rpcg, cuda, oracle_lib, seed):
     assert same(_exact_gpu(rpcg, a, b, cuda), oracle_lib.dot_exact(a, b))
 
 
+def _wide_values(rng, n, hi=1023):
+    """n doubles with exponents uniform over [-1074, hi] (subnormals below
+    -1022), random significands and signs."""
+    e = rng.integers(-1074, hi + 1, n)
+    m = rng.integers(0, 1 << 52, n, dtype=np.int64)
+    normal = np.ldexp((m | (1 << 52)).astype(np.float64), np.maximum(e, -1022) - 52)
+    sub = np.ldexp(m.astype(np.float64), np.full(n, -1074))
+    v = np.where(e < -1022, sub, normal)
+    return np.where(rng.random(n) < 0.5, -v, v)
+
+
+@pytest.mark.parametrize("n", [65536, 70001, 1000003])
+@pytest.mark.parametrize("layout", ["wide", "mixed"])
+def test_dot_exact_wide_exponents_large(rpcg, cuda, oracle_lib, n, layout):
+    """Products spread over the whole exponent range, at sizes with many
+    CTAs: every pair ("wide"), or every seventh pair among U[-1, 1] pairs
+    ("mixed": each thread's register windows keep moving); through both
+    entry points."""
+    rng = np.random.default_rng(n)
+    a, b = synth.dot_family_a(n, 17)
+    wa, wb = _wide_values(rng, n, hi=1000), _wide_values(rng, n, hi=0)
+    if layout == "wide":
+        a, b = wa, wb
+    else:
+        a[::7], b[::7] = wa[::7], wb[::7]
+    want = oracle_lib.dot_exact(a, b, nthreads=oracle_lib.default_threads())
+    assert math.isfinite(want)
+    assert same(_exact_gpu(rpcg, a, b, cuda), want)
+    assert same(rpcg.dot_exact_noalloc(_dev(a, cuda), _dev(b, cuda)).item(), want)
+
+
 def test_dot_exact_special_values(rpcg, cuda, oracle_lib):
     n = 3000
     a, b = synth.dot_family_a(n, 5)

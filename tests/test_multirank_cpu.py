@@ -45,6 +45,7 @@ def _work(rank, world, port, q):
 
     class A:
         side, stencil, steps, warmup, tol, band, band_n = 6, 7, 1, 1, 1e-8, 0, 0
+        variant, max_iter, gpus = "exblas", 1000, 2
 
     with contextlib.redirect_stdout(buf):
         bench.reference_arm(A, rank, world)
