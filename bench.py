@@ -70,7 +70,9 @@ def parse():
     ap.add_argument("--batch", type=int, default=0, metavar="COUNT",
                     help="only the batched workload: COUNT variable-diffusion systems, s ~ U{8..64}, tol 1e-10")
     ap.add_argument("--dot-only", type=int, default=0, metavar="LOG2N",
-                    help="only time the exact, fpe and plain dots on 2^LOG2N U[-1,1] pairs")
+                    help="only time the exact, fpe and plain dots on 2^LOG2N pairs of --dot-family")
+    ap.add_argument("--dot-family", default="a", choices=["a", "b", "c8", "c16", "c24", "c32", "c40"],
+                    help="pairs for --dot-only: (a) U[-1,1]; (b) m 2^e, e in [-300, 300]; (cK) cond 1eK")
     ap.add_argument("--eager", action="store_true",
                     help="launch the solver's kernels one by one instead of the graph (for profilers)")
     return ap.parse_args()
@@ -523,7 +525,8 @@ def gpu_arm(args, rank, world, local_rank):
 
 
 def dot_arm(args):
-    """--dot-only: the three dot products on 2^k U[-1,1] pairs (16 B per element)."""
+    """--dot-only: the three dot products on 2^k pairs of one family (16 B per
+    element; a draw of at most 2^24 pairs, tiled)."""
     import torch
 
     import paper_2005_07282_gb300 as P
@@ -532,7 +535,11 @@ def dot_arm(args):
     dev = torch.device("cuda", 0)
     n = 1 << args.dot_only
     base = min(n, 1 << 24)
-    a0, b0 = synth.dot_family_a(base, synth.BASE_SEED + 1)
+    fam = args.dot_family
+    if fam.startswith("c"):
+        a0, b0 = synth.dot_family_c(base, float("1e" + fam[1:]), synth.BASE_SEED + 5)
+    else:
+        a0, b0 = getattr(synth, f"dot_family_{fam}")(base, synth.BASE_SEED + 1)
     da = torch.from_numpy(a0).to(dev).repeat(n // base)
     db = torch.from_numpy(b0).to(dev).repeat(n // base)
     peak, kind = hbm_peak()
@@ -550,7 +557,7 @@ def dot_arm(args):
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / args.steps
         res[name] = {"ms": ms, "gbs": 16 * n / (ms * 1e-3) / 1e9, "frac": 16 * n / (ms * 1e-3) / 1e9 / peak}
-    print(json.dumps({"workload": f"dot U[-1,1] n=2^{args.dot_only}", "peak_gbs": peak, "peak_kind": kind,
+    print(json.dumps({"workload": f"dot family {fam} n=2^{args.dot_only}", "peak_gbs": peak, "peak_kind": kind,
                       "steps": args.steps, "warmup": args.warmup, **res}), flush=True)
 
 

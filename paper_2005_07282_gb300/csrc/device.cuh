@@ -133,19 +133,15 @@ __device__ __forceinline__ unsigned long long signed_chunk(uint32_t w, uint32_t 
 }
 
 // Deposit a product into a shared-memory accumulator laid out as
-// sacc[digit * C + copy] (64-bit atomics; wrap-around addition of
-// two's-complement values is exact while the true digit sum fits).  C
-// copies spread the atomics of a warp over the banks: with C = 32 and copy
-// = lane, a warp's 64-bit atomics take two conflict-free wavefronts
-// whatever digits its lanes hit.
-template <int C = kCopies>
+// sacc[digit * kCopies + copy] (64-bit atomics; wrap-around addition of
+// two's-complement values is exact while the true digit sum fits).
 __device__ __forceinline__ void smem_deposit(unsigned long long* sacc, int copy, const ExactProd& p) {
-  unsigned long long* base = sacc + p.q * C + copy;
-  if (p.w0) atomicAdd(base + 0 * C, signed_chunk(p.w0, p.neg));
-  if (p.w1) atomicAdd(base + 1 * C, signed_chunk(p.w1, p.neg));
-  if (p.w2) atomicAdd(base + 2 * C, signed_chunk(p.w2, p.neg));
-  if (p.w3) atomicAdd(base + 3 * C, signed_chunk(p.w3, p.neg));
-  if (p.w4) atomicAdd(base + 4 * C, signed_chunk(p.w4, p.neg));
+  unsigned long long* base = sacc + p.q * kCopies + copy;
+  if (p.w0) atomicAdd(base + 0 * kCopies, signed_chunk(p.w0, p.neg));
+  if (p.w1) atomicAdd(base + 1 * kCopies, signed_chunk(p.w1, p.neg));
+  if (p.w2) atomicAdd(base + 2 * kCopies, signed_chunk(p.w2, p.neg));
+  if (p.w3) atomicAdd(base + 3 * kCopies, signed_chunk(p.w3, p.neg));
+  if (p.w4) atomicAdd(base + 4 * kCopies, signed_chunk(p.w4, p.neg));
 }
 
 // Per-thread register window: a 224-bit two's-complement integer W whose
@@ -168,16 +164,15 @@ __device__ __forceinline__ void window_init(Window& w) {
   w.qb = kUnanchored;
 }
 
-template <int C = kCopies>
 __device__ __forceinline__ void window_flush(Window& w, unsigned long long* sacc, int copy) {
   if (w.qb < 0) return;
-  unsigned long long* base = sacc + w.qb * C + copy;
+  unsigned long long* base = sacc + w.qb * kCopies + copy;
 #pragma unroll
   for (int k = 0; k < kWin - 1; k++) {
-    if (w.W[k]) atomicAdd(base + k * C, (unsigned long long)w.W[k]);
+    if (w.W[k]) atomicAdd(base + k * kCopies, (unsigned long long)w.W[k]);
   }
   // the top word carries the sign of the whole window
-  if (w.W[kWin - 1]) atomicAdd(base + (kWin - 1) * C, (unsigned long long)(long long)(int)w.W[kWin - 1]);
+  if (w.W[kWin - 1]) atomicAdd(base + (kWin - 1) * kCopies, (unsigned long long)(long long)(int)w.W[kWin - 1]);
 #pragma unroll
   for (int k = 0; k < kWin; k++) w.W[k] = 0;
 }
@@ -208,7 +203,6 @@ __device__ __forceinline__ void window_add(Window& w, const ExactProd& p, bool t
       : "r"(m), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5));
 }
 
-template <int C = kCopies>
 __device__ __forceinline__ void exact_deposit(Window& w, unsigned long long* sacc, int copy, const ExactProd& p) {
   if (!p.nz) return;
   const int t = p.q - w.qb;
@@ -217,50 +211,23 @@ __device__ __forceinline__ void exact_deposit(Window& w, unsigned long long* sac
   } else if (t > 1) {
     // a larger product (or the first one): move the window up to it.  q is at
     // most 128, so the clamped anchor keeps q - qb in {0, 1}.
-    window_flush<C>(w, sacc, copy);
+    window_flush(w, sacc, copy);
     const int qb = min(max(p.q - 1, 0), kNDig - kWin);
     w.qb = qb;
     window_add(w, p, p.q - qb == 1);
   } else {
-    smem_deposit<C>(sacc, copy, p);
+    smem_deposit(sacc, copy, p);
   }
 }
 
-// exact_deposit with a second register window `lo` kept two digits below the
-// main one (for data whose products spread over more digit positions than
-// one window covers, e.g. wide exponent ranges): products one or two digits
-// below the main window go there instead of to shared memory.  Both windows
-// move together when a larger product arrives.
-template <int C = kCopies>
-__device__ __forceinline__ void exact_deposit_wide(Window& w, Window& lo, unsigned long long* sacc, int copy,
-                                                   const ExactProd& p) {
-  if (!p.nz) return;
-  const int t = p.q - w.qb;
-  if ((unsigned)t < 2u) {
-    window_add(w, p, t == 1);
-  } else if (t > 1) {
-    window_flush<C>(w, sacc, copy);
-    window_flush<C>(lo, sacc, copy);
-    const int qb = min(max(p.q - 1, 0), kNDig - kWin);
-    w.qb = qb;
-    lo.qb = qb >= 2 ? qb - 2 : kUnanchored;
-    window_add(w, p, p.q - qb == 1);
-  } else {
-    const int tl = p.q - lo.qb;
-    if ((unsigned)tl < 2u) window_add(lo, p, tl == 1);
-    else smem_deposit<C>(sacc, copy, p);
-  }
-}
-
-// Sum the C copies of each digit of a CTA's shared accumulator and add
+// Sum the kCopies copies of each digit of a CTA's shared accumulator and add
 // the non-zero digits to the global accumulator.  Needs a __syncthreads()
 // before (all deposits done) -- the caller provides it.
-template <int C = kCopies>
 __device__ __forceinline__ void smem_to_global(const unsigned long long* sacc, unsigned long long* gacc) {
   for (int k = threadIdx.x; k < kNDig; k += blockDim.x) {
     unsigned long long s = 0;
 #pragma unroll
-    for (int c = 0; c < C; c++) s += sacc[k * C + (c + k) % C];
+    for (int c = 0; c < kCopies; c++) s += sacc[k * kCopies + ((c + k) & (kCopies - 1))];  // staggered: fewer bank conflicts
     if (s) atomicAdd(gacc + k, s);
   }
   // make this thread's additions visible device-wide before the CTA announces
@@ -268,10 +235,9 @@ __device__ __forceinline__ void smem_to_global(const unsigned long long* sacc, u
   __threadfence();
 }
 
-// Zero `nacc` shared-memory accumulators (kNDig * C words each).
-template <int C = kCopies>
+// Zero `nacc` shared-memory accumulators (kNDig * kCopies words each).
 __device__ __forceinline__ void smem_acc_zero(unsigned long long* sacc, int nacc = 1) {
-  for (int k = threadIdx.x; k < nacc * kNDig * C; k += blockDim.x) sacc[k] = 0ull;
+  for (int k = threadIdx.x; k < nacc * kNDig * kCopies; k += blockDim.x) sacc[k] = 0ull;
 }
 
 // ------------------------------------------------------------------ rounding

@@ -51,15 +51,115 @@ struct DotScratch {
 constexpr size_t kDotScratchHeader = offsetof(DotScratch, partials);
 
 // ------------------------------------------------------------------ exact dot
-// Copies of the shared accumulator in k_dot_exact: one per lane, so that a
-// warp's shared-memory atomics never collide on a bank (34.8 KB a CTA).
-constexpr int kDotCopies = 32;
+// The shared accumulator of k_dot_exact holds kNHalf digits of 16 bits
+// (half digit h weighs 2^(16 h) units of the 32-bit digit grid), each a
+// signed 32-bit word, in 32 copies: sacc[h * 32 + lane].  Native 32-bit
+// shared atomics add to it (64-bit ones run about four times slower), and
+// with one copy per lane a warp's atomics never share a bank.  Each add is
+// below 2^16 in magnitude; a word takes at most 3 adds per product from
+// each of the BLOCK / 32 threads of its lane (the product's own chunk, and
+// the flush of both register windows, whose digits overlap, when they
+// move) and 2 more from each at the end, so spilling the words to the
+// global digits every kSpillProducts products per thread keeps every word's
+// sum below 2^31: (3 * 8 * 1024 + 16) * (2^16 - 1) < 2^31 at BLOCK = 256.
+constexpr int kNHalf = 2 * kNDig;
+constexpr int kSpillProducts = 1024;
 
-__device__ __forceinline__ void exact_step(Window& win, Window& lo, unsigned long long* sacc, int copy, bool& bad,
-                                           double x, double y) {
+__device__ __forceinline__ void half_add(uint32_t* at, uint32_t v, uint32_t neg) {
+  if (v) atomicAdd(at, (v ^ neg) - neg);
+}
+
+// A product that no register window takes: ten 16-bit chunks of its five
+// 32-bit words, at half digits 2q .. 2q + 9.
+__device__ __forceinline__ void half_deposit(uint32_t* sacc, const ExactProd& p) {
+  uint32_t* at = sacc + 2 * p.q * 32;
+  const uint32_t m = p.neg;
+  half_add(at + 0 * 32, p.w0 & 0xffffu, m);
+  half_add(at + 1 * 32, p.w0 >> 16, m);
+  half_add(at + 2 * 32, p.w1 & 0xffffu, m);
+  half_add(at + 3 * 32, p.w1 >> 16, m);
+  half_add(at + 4 * 32, p.w2 & 0xffffu, m);
+  half_add(at + 5 * 32, p.w2 >> 16, m);
+  half_add(at + 6 * 32, p.w3 & 0xffffu, m);
+  half_add(at + 7 * 32, p.w3 >> 16, m);
+  half_add(at + 8 * 32, p.w4 & 0xffffu, m);
+  half_add(at + 9 * 32, p.w4 >> 16, m);
+}
+
+// Empty a register window into the half digits 2 qb .. 2 qb + 13: its six
+// low words unsigned, the top word (the window's sign) as an unsigned low
+// half and a signed high half.
+__device__ __forceinline__ void half_flush(Window& w, uint32_t* sacc) {
+  if (w.qb < 0) return;
+  uint32_t* at = sacc + 2 * w.qb * 32;
+#pragma unroll
+  for (int k = 0; k < kWin - 1; k++) {
+    half_add(at + (2 * k) * 32, w.W[k] & 0xffffu, 0u);
+    half_add(at + (2 * k + 1) * 32, w.W[k] >> 16, 0u);
+  }
+  half_add(at + (2 * kWin - 2) * 32, w.W[kWin - 1] & 0xffffu, 0u);
+  half_add(at + (2 * kWin - 1) * 32, (uint32_t)((int32_t)w.W[kWin - 1] >> 16), 0u);
+#pragma unroll
+  for (int k = 0; k < kWin; k++) w.W[k] = 0;
+}
+
+// Two register windows per thread: `w` over digits qb .. qb + 6 and `lo`
+// two digits below it.  A product whose digit index is in {qb, qb + 1} goes
+// to w, in {qb - 2, qb - 1} to lo, anything else to the shared half digits.
+// A product above w also raises `qtop`; the windows move up to it only at
+// the end of a round of products (half_reanchor), so that the flush code
+// exists once in the loop instead of once per product of the round (inlined
+// eight times it overflowed the instruction cache).
+__device__ __forceinline__ void half_exact_deposit(Window& w, Window& lo, uint32_t* sacc, int& qtop,
+                                                   const ExactProd& p) {
+  if (!p.nz) return;
+  const int t = p.q - w.qb;
+  if ((unsigned)t < 2u) {
+    window_add(w, p, t == 1);
+  } else if ((unsigned)(t + 2) < 2u) {
+    window_add(lo, p, t == -1);
+  } else {
+    half_deposit(sacc, p);
+    if (t > 1) qtop = max(qtop, p.q);
+  }
+}
+
+// Move both windows up to the largest product seen above them (if any).
+__device__ __forceinline__ void half_reanchor(Window& w, Window& lo, uint32_t* sacc, int& qtop) {
+  if (qtop < 0) return;
+  half_flush(w, sacc);
+  half_flush(lo, sacc);
+  // qb >= 2 keeps lo anchored at digit 0 or above; q <= kNDig - 5 for every
+  // product, so q - qb stays in {0, 1} below the upper clamp too
+  const int qb = min(max(qtop - 1, 2), kNDig - kWin);
+  w.qb = qb;
+  lo.qb = qb - 2;
+  qtop = -1;
+}
+
+// Add the 32 copies of every half digit to the global 32-bit digits (half
+// digit h goes to digit h / 2, shifted up 16 bits when h is odd); with
+// `clear`, zero the copies for the next spill interval.  Needs a
+// __syncthreads() before (deposits done) and, with `clear`, one after.
+__device__ __forceinline__ void half_to_global(uint32_t* sacc, unsigned long long* gacc, bool clear) {
+  for (int h = threadIdx.x; h < kNHalf; h += blockDim.x) {
+    long long s = 0;
+#pragma unroll 8
+    for (int c = 0; c < 32; c++) {
+      uint32_t* at = sacc + h * 32 + ((c + h) & 31);
+      s += (int32_t)*at;
+      if (clear) *at = 0u;
+    }
+    if (s) atomicAdd(gacc + (h >> 1), (unsigned long long)(s * ((h & 1) ? 65536ll : 1ll)));
+  }
+  __threadfence();
+}
+
+__device__ __forceinline__ void exact_step(Window& win, Window& lo, uint32_t* sacc, int& qtop, bool& bad, double x,
+                                           double y) {
   const ExactProd p = exact_product(x, y);
   bad |= p.bad;
-  exact_deposit_wide<kDotCopies>(win, lo, sacc, copy, p);
+  half_exact_deposit(win, lo, sacc, qtop, p);
 }
 
 // The last CTA: normalise, round once, publish, leave the scratch clean.
@@ -76,32 +176,37 @@ static __device__ __noinline__ void dot_exact_finish(DotScratch* ws, double* out
 
 // ALIGNED: a and b start on 16-byte boundaries (pairs of elements are
 // loaded as double2); the host picks the instance.  Each thread keeps two
-// register windows of digits (exact_deposit_wide), so products spread over
+// register windows of digits (half_exact_deposit), so products spread over
 // up to four digit positions stay in registers: on U[-1, 1] pairs, whose
 // products all fit the first window, the second one costs about 2% against
 // a one-window kernel; on ill-conditioned pairs (cond 1e16 to 1e32) it
-// halves the time.
+// halves the time.  The loops run the same number of times in every thread
+// of a CTA, so that the spills' barriers are reached by all.
 template <int BLOCK, bool ALIGNED>
 __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, DotScratch* ws, double* out) {
-  __shared__ unsigned long long sacc[kNDig * kDotCopies];
+  static_assert(BLOCK == 256, "the spill bound assumes 8 threads per lane copy");
+  __shared__ uint32_t sacc[kNHalf * 32];
   __shared__ long long sdig[kNDig];
   __shared__ uint32_t sD[kNDig];
-  smem_acc_zero<kDotCopies>(sacc);
+  for (int k = threadIdx.x; k < kNHalf * 32; k += BLOCK) sacc[k] = 0u;
   __syncthreads();
   Window win, lo;
   window_init(win);
   window_init(lo);
-  const int copy = threadIdx.x & (kDotCopies - 1);
+  uint32_t* sl = sacc + (threadIdx.x & 31);  // this lane's copy
+  int qtop = -1;
   bool bad = false;
-  const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * BLOCK;
+  int64_t i0 = (int64_t)blockIdx.x * BLOCK;  // the CTA's first index of the current round
+  int since = 0;                             // products per thread since the last spill
   if constexpr (ALIGNED) {
     const double2* a2 = reinterpret_cast<const double2*>(a);
     const double2* b2 = reinterpret_cast<const double2*>(b);
     const int64_t n2 = n >> 1;
-    int64_t i = tid;
-    for (; i + 3 * nthr < n2; i += 4 * nthr) {
+    // rounds of 8 products per thread, while every thread of the CTA has them
+    for (; i0 + (BLOCK - 1) + 3 * nthr < n2; i0 += 4 * nthr) {
+      const int64_t i = i0 + threadIdx.x;
       double2 x[4], y[4];
 #pragma unroll
       for (int u = 0; u < 4; u++) {
@@ -110,24 +215,43 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
       }
 #pragma unroll
       for (int u = 0; u < 4; u++) {
-        exact_step(win, lo, sacc, copy, bad, x[u].x, y[u].x);
-        exact_step(win, lo, sacc, copy, bad, x[u].y, y[u].y);
+        exact_step(win, lo, sl, qtop, bad, x[u].x, y[u].x);
+        exact_step(win, lo, sl, qtop, bad, x[u].y, y[u].y);
+      }
+      half_reanchor(win, lo, sl, qtop);
+      since += 8;
+      if (since > kSpillProducts - 8 - 9) {
+        __syncthreads();
+        half_to_global(sacc, ws->digits, true);
+        __syncthreads();
+        since = 0;
       }
     }
-    for (; i < n2; i += nthr) {
+    // the rest: at most 4 pairs per thread, and the odd last element
+    for (int64_t i = i0 + threadIdx.x; i < n2; i += nthr) {
       const double2 x = __ldcs(a2 + i), y = __ldcs(b2 + i);
-      exact_step(win, lo, sacc, copy, bad, x.x, y.x);
-      exact_step(win, lo, sacc, copy, bad, x.y, y.y);
+      exact_step(win, lo, sl, qtop, bad, x.x, y.x);
+      exact_step(win, lo, sl, qtop, bad, x.y, y.y);
     }
-    if ((n & 1) && tid == 0) exact_step(win, lo, sacc, copy, bad, a[n - 1], b[n - 1]);
+    if ((n & 1) && blockIdx.x == 0 && threadIdx.x == 0) exact_step(win, lo, sl, qtop, bad, a[n - 1], b[n - 1]);
   } else {
-    for (int64_t i = tid; i < n; i += nthr) exact_step(win, lo, sacc, copy, bad, a[i], b[i]);
+    for (; i0 < n; i0 += nthr) {
+      const int64_t i = i0 + threadIdx.x;
+      if (i < n) exact_step(win, lo, sl, qtop, bad, a[i], b[i]);
+      half_reanchor(win, lo, sl, qtop);
+      if (++since == kSpillProducts) {
+        __syncthreads();
+        half_to_global(sacc, ws->digits, true);
+        __syncthreads();
+        since = 0;
+      }
+    }
   }
-  window_flush<kDotCopies>(win, sacc, copy);
-  window_flush<kDotCopies>(lo, sacc, copy);
+  half_flush(win, sl);
+  half_flush(lo, sl);
   if (bad) atomicOr(&ws->flags, 1u);
   __syncthreads();
-  smem_to_global<kDotCopies>(sacc, ws->digits);
+  half_to_global(sacc, ws->digits, false);
   if (is_last_block(&ws->counter)) dot_exact_finish(ws, out, sdig, sD);
 }
 
