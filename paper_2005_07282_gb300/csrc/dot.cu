@@ -56,34 +56,122 @@ constexpr size_t kDotScratchHeader = offsetof(DotScratch, partials);
 // signed 32-bit word, in 32 copies: sacc[h * 32 + lane].  Native 32-bit
 // shared atomics add to it (64-bit ones run about four times slower), and
 // with one copy per lane a warp's atomics never share a bank.  Each add is
-// below 2^16 in magnitude; a word takes at most 3 adds per product from
+// at most 2^16 in magnitude; a word takes at most 3 adds per product from
 // each of the BLOCK / 32 threads of its lane (the product's own chunk, and
 // the flush of both register windows, whose digits overlap, when they
 // move) and 2 more from each at the end, so spilling the words to the
 // global digits every kSpillProducts products per thread keeps every word's
-// sum below 2^31: (3 * 8 * 1024 + 16) * (2^16 - 1) < 2^31 at BLOCK = 256.
+// sum below 2^31: (3 * 8 * 1024 + 16) * 2^16 < 2^31 at BLOCK = 256.
 constexpr int kNHalf = 2 * kNDig;
 constexpr int kSpillProducts = 1024;
 
-__device__ __forceinline__ void half_add(uint32_t* at, uint32_t v, uint32_t neg) {
-  if (v) atomicAdd(at, (v ^ neg) - neg);
+// A product in complemented form: |a b| shifted left by its in-digit
+// offset, in five words, all bits flipped when the product is negative.
+// With m below and above them (bits shifted in and the sign extension) and
+// a carry-in of m & 1, adding these words adds the signed product in two's
+// complement; the flip is done on the four product words before the shift
+// instead of on the six words of every window add.
+struct WinProd {
+  uint32_t w0, w1, w2, w3, w4;
+  int q;       // digit index of w0
+  uint32_t m;  // all ones for a negative product
+  bool nz;     // false only for a non-finite operand
+  bool bad;    // a or b is Inf or NaN
+};
+
+__device__ __forceinline__ WinProd win_product(double a, double b) {
+  const uint32_t ah = (uint32_t)__double2hiint(a), al = (uint32_t)__double2loint(a);
+  const uint32_t bh = (uint32_t)__double2hiint(b), bl = (uint32_t)__double2loint(b);
+  const uint32_t fa = ah & 0x7ff00000u, fb = bh & 0x7ff00000u;
+  WinProd p;
+  // field 0 wraps to 0xfff00000, field 0x7ff to 0x7fe00000: both outside the normal range
+  if ((fa - 0x00100000u) >= 0x7fe00000u || (fb - 0x00100000u) >= 0x7fe00000u) {
+    const ExactProd e = exact_product_general(a, b);
+    p.w0 = e.w0 ^ e.neg;
+    p.w1 = e.w1 ^ e.neg;
+    p.w2 = e.w2 ^ e.neg;
+    p.w3 = e.w3 ^ e.neg;
+    p.w4 = e.w4 ^ e.neg;
+    p.q = e.q;
+    p.m = e.neg;
+    p.nz = e.nz;
+    p.bad = e.bad;
+    return p;
+  }
+  p.bad = false;
+  p.nz = true;
+  const uint32_t m = (uint32_t)((int32_t)(ah ^ bh) >> 31);
+  const uint32_t mah = (ah & 0x000FFFFFu) | 0x00100000u;
+  const uint32_t mbh = (bh & 0x000FFFFFu) | 0x00100000u;
+  // offset of the product's lowest bit from 2^kE0 (28 .. 4118; fa + fb < 2^32);
+  // the funnel shifts take it modulo 32
+  const uint32_t o = ((fa + fb) >> 20) - (uint32_t)(2150 + kE0);
+  p.q = (int)(o >> 5);
+  const uint64_t p0 = (uint64_t)al * bl;
+  const uint64_t p1 = (uint64_t)al * mbh + (uint64_t)mah * bl;  // < 2^54
+  const uint64_t p2 = (uint64_t)mah * mbh;                      // < 2^42
+  uint32_t v1, v2, v3;
+  asm("add.cc.u32 %0, %3, %4;\n\t"
+      "addc.cc.u32 %1, %5, %6;\n\t"
+      "addc.u32 %2, %7, 0;"
+      : "=r"(v1), "=r"(v2), "=r"(v3)
+      : "r"((uint32_t)(p0 >> 32)), "r"((uint32_t)p1), "r"((uint32_t)(p1 >> 32)), "r"((uint32_t)p2),
+        "r"((uint32_t)(p2 >> 32)));
+  const uint32_t c0 = (uint32_t)p0 ^ m, c1 = v1 ^ m, c2 = v2 ^ m, c3 = v3 ^ m;
+  p.w0 = __funnelshift_l(m, c0, o);
+  p.w1 = __funnelshift_l(c0, c1, o);
+  p.w2 = __funnelshift_l(c1, c2, o);
+  p.w3 = __funnelshift_l(c2, c3, o);
+  p.w4 = __funnelshift_l(c3, m, o);
+  p.m = m;
+  return p;
 }
 
-// A product that no register window takes: ten 16-bit chunks of its five
-// 32-bit words, at half digits 2q .. 2q + 9.
-__device__ __forceinline__ void half_deposit(uint32_t* sacc, const ExactProd& p) {
+// W += the signed product at word offset t1 (0 or 1) in the window.
+__device__ __forceinline__ void window_add_c(Window& w, const WinProd& p, bool t1) {
+  const uint32_t m = p.m;
+  const uint32_t a0 = t1 ? m : p.w0;
+  const uint32_t a1 = t1 ? p.w0 : p.w1;
+  const uint32_t a2 = t1 ? p.w1 : p.w2;
+  const uint32_t a3 = t1 ? p.w2 : p.w3;
+  const uint32_t a4 = t1 ? p.w3 : p.w4;
+  const uint32_t a5 = t1 ? p.w4 : m;
+  asm("{\n\t"
+      ".reg .u32 t;\n\t"
+      "add.cc.u32 t, %7, %7;\n\t"
+      "addc.cc.u32 %0, %0, %8;\n\t"
+      "addc.cc.u32 %1, %1, %9;\n\t"
+      "addc.cc.u32 %2, %2, %10;\n\t"
+      "addc.cc.u32 %3, %3, %11;\n\t"
+      "addc.cc.u32 %4, %4, %12;\n\t"
+      "addc.cc.u32 %5, %5, %13;\n\t"
+      "addc.u32 %6, %6, %7;\n\t"
+      "}"
+      : "+r"(w.W[0]), "+r"(w.W[1]), "+r"(w.W[2]), "+r"(w.W[3]), "+r"(w.W[4]), "+r"(w.W[5]), "+r"(w.W[6])
+      : "r"(m), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5));
+}
+
+// A product that no register window takes: the ten 16-bit chunks of its
+// five words at half digits 2q .. 2q + 9 (the lowest with the carry-in
+// m & 1), and m at 2q + 10 for the all-ones bits above them.  No test for
+// zero chunks: a predicate costs as much issue as the atomic it would skip.
+__device__ __forceinline__ void half_deposit(uint32_t* sacc, const WinProd& p) {
   uint32_t* at = sacc + 2 * p.q * 32;
-  const uint32_t m = p.neg;
-  half_add(at + 0 * 32, p.w0 & 0xffffu, m);
-  half_add(at + 1 * 32, p.w0 >> 16, m);
-  half_add(at + 2 * 32, p.w1 & 0xffffu, m);
-  half_add(at + 3 * 32, p.w1 >> 16, m);
-  half_add(at + 4 * 32, p.w2 & 0xffffu, m);
-  half_add(at + 5 * 32, p.w2 >> 16, m);
-  half_add(at + 6 * 32, p.w3 & 0xffffu, m);
-  half_add(at + 7 * 32, p.w3 >> 16, m);
-  half_add(at + 8 * 32, p.w4 & 0xffffu, m);
-  half_add(at + 9 * 32, p.w4 >> 16, m);
+  atomicAdd(at + 0 * 32, (p.w0 & 0xffffu) + (p.m & 1u));
+  atomicAdd(at + 1 * 32, p.w0 >> 16);
+  atomicAdd(at + 2 * 32, p.w1 & 0xffffu);
+  atomicAdd(at + 3 * 32, p.w1 >> 16);
+  atomicAdd(at + 4 * 32, p.w2 & 0xffffu);
+  atomicAdd(at + 5 * 32, p.w2 >> 16);
+  atomicAdd(at + 6 * 32, p.w3 & 0xffffu);
+  atomicAdd(at + 7 * 32, p.w3 >> 16);
+  atomicAdd(at + 8 * 32, p.w4 & 0xffffu);
+  atomicAdd(at + 9 * 32, p.w4 >> 16);
+  atomicAdd(at + 10 * 32, p.m);
+}
+
+__device__ __forceinline__ void half_add(uint32_t* at, uint32_t v) {
+  if (v) atomicAdd(at, v);
 }
 
 // Empty a register window into the half digits 2 qb .. 2 qb + 13: its six
@@ -94,11 +182,11 @@ __device__ __forceinline__ void half_flush(Window& w, uint32_t* sacc) {
   uint32_t* at = sacc + 2 * w.qb * 32;
 #pragma unroll
   for (int k = 0; k < kWin - 1; k++) {
-    half_add(at + (2 * k) * 32, w.W[k] & 0xffffu, 0u);
-    half_add(at + (2 * k + 1) * 32, w.W[k] >> 16, 0u);
+    half_add(at + (2 * k) * 32, w.W[k] & 0xffffu);
+    half_add(at + (2 * k + 1) * 32, w.W[k] >> 16);
   }
-  half_add(at + (2 * kWin - 2) * 32, w.W[kWin - 1] & 0xffffu, 0u);
-  half_add(at + (2 * kWin - 1) * 32, (uint32_t)((int32_t)w.W[kWin - 1] >> 16), 0u);
+  half_add(at + (2 * kWin - 2) * 32, w.W[kWin - 1] & 0xffffu);
+  half_add(at + (2 * kWin - 1) * 32, (uint32_t)((int32_t)w.W[kWin - 1] >> 16));
 #pragma unroll
   for (int k = 0; k < kWin; k++) w.W[k] = 0;
 }
@@ -111,13 +199,13 @@ __device__ __forceinline__ void half_flush(Window& w, uint32_t* sacc) {
 // exists once in the loop instead of once per product of the round (inlined
 // eight times it overflowed the instruction cache).
 __device__ __forceinline__ void half_exact_deposit(Window& w, Window& lo, uint32_t* sacc, int& qtop,
-                                                   const ExactProd& p) {
+                                                   const WinProd& p) {
   if (!p.nz) return;
   const int t = p.q - w.qb;
   if ((unsigned)t < 2u) {
-    window_add(w, p, t == 1);
+    window_add_c(w, p, t == 1);
   } else if ((unsigned)(t + 2) < 2u) {
-    window_add(lo, p, t == -1);
+    window_add_c(lo, p, t == -1);
   } else {
     half_deposit(sacc, p);
     if (t > 1) qtop = max(qtop, p.q);
@@ -157,7 +245,7 @@ __device__ __forceinline__ void half_to_global(uint32_t* sacc, unsigned long lon
 
 __device__ __forceinline__ void exact_step(Window& win, Window& lo, uint32_t* sacc, int& qtop, bool& bad, double x,
                                            double y) {
-  const ExactProd p = exact_product(x, y);
+  const WinProd p = win_product(x, y);
   bad |= p.bad;
   half_exact_deposit(win, lo, sacc, qtop, p);
 }
