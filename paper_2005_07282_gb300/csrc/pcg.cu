@@ -1043,6 +1043,21 @@ __global__ void k_check_csr(int n, int nnz, const int* rowptr, const int* col, i
   }
 }
 
+// The longest row of every 32-row slice (rows past n count as empty): one
+// warp per slice, one lane per row.  Run after k_check_csr found the row
+// pointers valid (the lengths are then non-negative).
+__global__ void k_slice_len(int n, const int* __restrict__ rowptr, int* __restrict__ len) {
+  const int nsl = (n + 31) / 32;
+  const int lane = threadIdx.x & 31;
+  const int warps = (gridDim.x * blockDim.x) >> 5;
+  for (int sl = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; sl < nsl; sl += warps) {
+    const int row = 32 * sl + lane;
+    const int l = row < n ? rowptr[row + 1] - rowptr[row] : 0;
+    const int m = __reduce_max_sync(0xffffffffu, l);
+    if (lane == 0) len[sl] = m;
+  }
+}
+
 // Scatter CSR rows into the SELL-32 layout (entry k of row i at
 // sptr[i / 32] + 32 k + i % 32), keeping each row's storage order.
 __global__ void k_csr_to_sell(int n, const int* __restrict__ rowptr, const int* __restrict__ ccol,
@@ -1158,7 +1173,10 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
   if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(ccol, col, (size_t)nnz * sizeof(int), kind, s);
   if (e == cudaSuccess && nnz) e = cudaMemcpyAsync(cval, val, (size_t)nnz * sizeof(double), kind, s);
   if (e == cudaSuccess) e = cudaMemsetAsync(A->scratch, 0, offsetof(PassScratch, partials), s);
-  // 2. validate on the device (monotone row pointers, columns in range)
+  // 2. validate on the device (monotone row pointers, columns in range) and
+  // take every slice's longest row there
+  const int nslices = (n + 31) / 32;
+  std::vector<int> hlen((size_t)nslices);
   if (e == cudaSuccess) {
     int* bad = nullptr;
     e = cudaMallocAsync((void**)&bad, sizeof(int), s);
@@ -1170,8 +1188,18 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, sizeof(int), cudaMemcpyDeviceToHost, s);
-    if (bad) cudaFreeAsync(bad, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess && !hbad && nslices > 0) {
+      // the lengths pass through the w vector, which is not in use yet
+      // (n doubles hold the n / 32 + 1 ints)
+      int* dlen = reinterpret_cast<int*>(A->w);
+      k_slice_len<<<sm_count() * 4, 256, 0, s>>>(n, A->rowptr, dlen);
+      e = cudaGetLastError();
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(hlen.data(), dlen, (size_t)nslices * sizeof(int), cudaMemcpyDeviceToHost, s);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    }
+    if (bad) cudaFreeAsync(bad, s);
     if (e == cudaSuccess && hbad) {
       free_tmp();
       destroy_handle(A);
@@ -1179,25 +1207,9 @@ rpcg_status rpcg_create(rpcg_matrix_t* A_out, int32_t n, int32_t nnz, const int3
       return RPCG_ERR_INVALID;
     }
   }
-  // 3. SELL-32 slice offsets on the host from the (now validated) row pointers
-  const int nslices = (n + 31) / 32;
+  // 3. SELL-32 slice offsets: 32 times the running sum of the longest rows
   std::vector<long long> hsptr((size_t)nslices + 1, 0);
-  if (e == cudaSuccess) {
-    std::vector<int> hrp;
-    const int* rp = rowptr;
-    if (ptr_kind == 1) {
-      hrp.resize((size_t)n + 1);
-      e = cudaMemcpyAsync(hrp.data(), A->rowptr, ((size_t)n + 1) * sizeof(int), cudaMemcpyDeviceToHost, s);
-      if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-      rp = hrp.data();
-    }
-    for (int sl = 0; sl < nslices && e == cudaSuccess; sl++) {
-      int len = 0;
-      const int r1 = std::min(n, 32 * sl + 32);
-      for (int i = 32 * sl; i < r1; i++) len = std::max(len, rp[i + 1] - rp[i]);
-      hsptr[sl + 1] = hsptr[sl] + 32ll * len;
-    }
-  }
+  for (int sl = 0; sl < nslices && e == cudaSuccess; sl++) hsptr[sl + 1] = hsptr[sl] + 32ll * hlen[sl];
   const long long total = hsptr[nslices];
   if (e == cudaSuccess) {
     st = alloc_dev((void**)&A->sptr, ((size_t)nslices + 1) * sizeof(long long));
