@@ -417,11 +417,20 @@ __global__ void __launch_bounds__(BLOCK, kFpeDotWarps * 32 / BLOCK) k_dot_fpe(in
   bool lost = false, nonfinite = false;
   const int64_t tid = (int64_t)blockIdx.x * BLOCK + threadIdx.x;
   const int64_t nthr = (int64_t)gridDim.x * BLOCK;
-  // compute-bound: no loads run ahead, which keeps registers for more warps
-  for (int64_t i = tid; i < n; i += nthr) {
-    const double x = __ldcs(a + i), y = __ldcs(b + i);
-    if (!is_finite_bits(x) || !is_finite_bits(y)) nonfinite = true;
-    else lost |= fpe_dot_step(res, err, p, x, y, nonfinite);
+  // compute-bound: no loads run ahead, which keeps registers for more warps.
+  // The loop runs the same number of times in every lane of a warp and the
+  // lanes meet at the end of each element: left to themselves after the
+  // cascades' divergent exits, they drifted apart and every FP64 addition
+  // was issued once per group of lanes instead of once per warp.
+  const int64_t lane = threadIdx.x & 31;
+  for (int64_t i0 = tid - lane; i0 < n; i0 += nthr) {
+    const int64_t i = i0 + lane;
+    if (i < n) {
+      const double x = __ldcs(a + i), y = __ldcs(b + i);
+      if (!is_finite_bits(x) || !is_finite_bits(y)) nonfinite = true;
+      else lost |= fpe_dot_step(res, err, p, x, y, nonfinite);
+    }
+    __syncwarp();
   }
   bool ovf = false;
   lost |= fpe_sum(res, err, p, ovf);
