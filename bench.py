@@ -106,9 +106,9 @@ PASS_A_TRAFFIC_RATIO = 702.0 / 710.9
 # full-set capture summarised in profiles/k_fpe_dots_p27_128.md (27-point
 # 128^3, percent of each pipe's own peak while the SMs are active).  The
 # FP64 pipe, half rate on this GPU, is the busiest unit: the fpe roof.
-FPE_PIPES = {"k_pass_a_dot": {"fp64": 75.1, "alu": 55.3, "issue": 49.2},
-             "k_pass_b1": {"fp64": 75.2, "alu": 46.4, "issue": 43.0},
-             "k_pass_b2": {"fp64": 73.4, "alu": 60.7, "issue": 53.2}}
+FPE_PIPES = {"k_pass_a_dot": {"fp64": 52.1, "alu": 62.0, "issue": 61.3},
+             "k_pass_b1": {"fp64": 62.9, "alu": 54.3, "issue": 55.2},
+             "k_pass_b2": {"fp64": 53.3, "alu": 61.0, "issue": 61.6}}
 
 
 def wl_name(args):
@@ -436,7 +436,8 @@ def gpu_arm(args, rank, world, local_rank):
         extras["pass_ms_fpe"] = {k: pf["pass_ms"][k] / lf for k in ("A", "B", "C")}
         fpe_ms = 1e3 / extras["fpe_iters_per_s"]
         extras["fpe_roofline"] = {
-            "bound": "fp64", "kernels": "k_pass_a_dot, k_pass_b1, k_pass_b2 (the iteration's three FPE dots)",
+            "bound": "issue (FP64 and ALU pipes each 52-63% busy)",
+            "kernels": "k_pass_a_dot, k_pass_b1, k_pass_b2 (the iteration's three FPE dots)",
             "pipe_active_pct": FPE_PIPES, "source": "ncu --set full, 27-point 128^3 (profiles/k_fpe_dots_p27_128.md)",
             "iteration_ms": fpe_ms, "iteration_hbm_frac": iter_bytes(n, nnz) / (fpe_ms * 1e-3) / 1e9 / hbm_peak()[0],
             "overhead_vs_plain": plain_rate / extras["fpe_iters_per_s"]}
