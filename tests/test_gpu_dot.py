@@ -207,6 +207,31 @@ def test_dot_fpe_integer_and_fp64_warps_agree(rpcg, cuda, oracle_lib, p):
             assert same(v.item(), oracle_lib.dot_exact(a, b))
 
 
+@pytest.mark.parametrize("p", [2, 3, 8])
+def test_dot_fpe_one_thread_random_exponents(rpcg, cuda, oracle_lib, p):
+    """The twosums of both expansions on products spread over the whole
+    exponent range (subnormal and near-overflow ones included), with equal
+    and opposite products, products that are exact powers of two and
+    operands of equal magnitude among them: 16 products in one thread
+    against the oracle's one-thread FPE dot, value and flag bit for bit."""
+    for seed in range(40):
+        rng = np.random.default_rng(1000 + seed)
+        k = 16
+        hi = 1000 if seed % 4 else 1023  # every fourth set may overflow
+        va = _wide_values(rng, k, hi=hi // 2)
+        vb = _wide_values(rng, k, hi=hi // 2)
+        if seed % 3 == 0:  # pairs that cancel exactly
+            va[1::2] = -va[0::2]
+            vb[1::2] = vb[0::2]
+        if seed % 5 == 0:  # powers of two of one magnitude
+            va[:8] = np.ldexp(1.0, rng.integers(-60, 60, 8)) * np.where(rng.random(8) < 0.5, -1, 1)
+            vb[:8] = np.ldexp(1.0, rng.integers(-60, 60, 8))
+        a, b = _one_thread(va, vb, 37, n=4096)
+        v, ex = rpcg.dot_fpe(_dev(a, cuda), _dev(b, cuda), p=p)
+        want_v, want_ex = oracle_lib.dot_fpe(a, b, p=p, T=1)
+        assert same(v.item(), want_v) and ex.item() == int(want_ex), (seed, v.item(), ex.item(), want_v, want_ex)
+
+
 @pytest.mark.parametrize("cond", [1e8, 1e24, 1e40])
 @pytest.mark.parametrize("p", [1, 2, 3, 8])
 def test_dot_fpe_one_thread_equals_oracle_fpe(rpcg, cuda, oracle_lib, cond, p):
