@@ -196,8 +196,8 @@ __host__ __device__ constexpr size_t b_smem(int nacc, int count) {
 // row2_fn(ctx, ra, rb, dep) does rows ra and rb together (both in range);
 // pass a NullRow2 to process rows one at a time.  skip_fn(sys) == true
 // skips a system's units altogether (no deposit, no arrival, no fin_fn).
-// fpe: twoprod in FP64, the Accumulate cascades with two_sum_split (one FP64
-// addition per twosum, the error on the integer pipe).
+// fpe: fpe_dot_step (twoprod on the integer pipe, the Accumulate cascades
+// with two_sum_fast in the result and two_sum_split in the error expansion).
 struct NullRow2 {};
 struct NoSkip {
   __device__ bool operator()(int) const { return false; }

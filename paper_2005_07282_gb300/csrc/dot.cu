@@ -399,9 +399,10 @@ __global__ void k_eft(int64_t n, const double* __restrict__ a, const double* __r
 // accumulator and are rounded once, so the merge loses nothing and *exact
 // reports whether any thread's expansion lost bits (or a product fell below
 // twoprod's exact range).  twoprod runs on the integer pipe
-// (two_prod_int), each twosum of the Accumulate cascades takes one FP64
-// addition with its error computed on the integer pipe (two_sum_split):
-// GB300's FP64 pipe is half rate.
+// (two_prod_int); the result expansion's twosums are Fast2Sum (three FP64
+// additions) and the error expansion's take one FP64 addition with the
+// error computed on the integer pipe (two_sum_split), which shares the
+// work between GB300's scarce FP64 pipe and the integer pipes.
 constexpr int kFpeDotWarps = 32;  // 64 registers (24 and 16 warps per SM measured slower)
 template <int BLOCK>
 __global__ void __launch_bounds__(BLOCK, kFpeDotWarps * 32 / BLOCK) k_dot_fpe(int64_t n, const double* __restrict__ a,

@@ -96,8 +96,8 @@ __device__ __forceinline__ FinalScratch* red_carve(unsigned char* base, unsigned
   return fs;
 }
 
-// fpe: twoprod in FP64, the Accumulate cascades with two_sum_split (one FP64
-// addition per twosum, the error on the integer pipe).
+// fpe: fpe_dot_step (twoprod on the integer pipe, the Accumulate cascades
+// with two_sum_fast in the result and two_sum_split in the error expansion).
 template <int V, int NACC>
 __device__ __forceinline__ void red_add(Reducer<V, NACC>& R, unsigned long long* sacc, int j, double a, double b,
                                         int p) {
