@@ -190,9 +190,11 @@ rpcg_status rpcg_dot_fpe(int64_t n, const double *a, const double *b, int32_t p,
 /*
  * rpcg_eft_twosum / rpcg_eft_twoprod -- the error-free transformations of
  * Alg. 1 (r = RN(a_i + b_i), s = a_i + b_i - r) and Alg. 2 (r = RN(a_i b_i),
- * s = fma(a_i, b_i, -r)) applied elementwise, with the FPE dot's own
- * arithmetic: twosum of finite elements as one FP64 addition with the
- * error computed exactly on the integer pipe (elements that are not finite,
+ * s = fma(a_i, b_i, -r)) applied elementwise, with the FPE dot's
+ * integer-pipe arithmetic: twosum of finite elements as one FP64 addition
+ * with the error computed exactly on the integer pipe (the form of the FPE
+ * dot's error expansion; its result expansion uses the FP64 Fast2Sum, whose
+ * pairs are the same) (elements that are not finite,
  * or whose sum overflows, use the FP64 formulas); twoprod of normal
  * elements whose product lies in [2^-916, 2^1023) as exact integer
  * arithmetic, others with the FP64 formulas.  Every output equals the FP64
