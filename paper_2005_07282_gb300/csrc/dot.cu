@@ -321,6 +321,8 @@ __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __
       }
       half_reanchor(win, lo, sl, qtop);
       since += 8;
+      // spill while there is room for one more round (8 products) and the
+      // rest after the loop (at most 9), so no interval exceeds kSpillProducts
       if (since > kSpillProducts - 8 - 9) {
         __syncthreads();
         half_to_global(sacc, ws->digits, true);
