@@ -30,6 +30,19 @@ def test_exact_dot_2p28(rpcg, cuda, oracle_lib, fam):
     assert bits([got])[0] == bits([want])[0]
 
 
+def test_exact_dot_2p28_unaligned_view(rpcg, cuda, oracle_lib):
+    """The instance for operands not on 16-byte boundaries (one element at a
+    time) at the full size, where every thread spills its shared digits to
+    the global ones more than once."""
+    import torch
+    n = 1 << 28
+    a, b = synth.dot_family_a(n + 1, synth.BASE_SEED + 4)
+    want = oracle_lib.dot_exact(a[1:], b[1:], nthreads=oracle_lib.default_threads())
+    ta, tb = torch.from_numpy(a).to(cuda), torch.from_numpy(b).to(cuda)
+    got = rpcg.dot_exact(ta[1:], tb[1:]).item()
+    assert bits([got])[0] == bits([want])[0]
+
+
 def test_exact_dot_family_c_2p26(rpcg, cuda, oracle_lib):
     import torch
     a, b = synth.dot_family_c(1 << 26, 1e32, synth.BASE_SEED + 1)
