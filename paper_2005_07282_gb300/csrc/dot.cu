@@ -238,20 +238,27 @@ __device__ __forceinline__ void half_reanchor(Window& w, Window& lo, uint32_t* s
   qtop = -1;
 }
 
-// Add the 32 copies of every half digit to the global 32-bit digits (half
-// digit h goes to digit h / 2, shifted up 16 bits when h is odd); with
-// `clear`, zero the copies for the next spill interval.  Needs a
-// __syncthreads() before (deposits done) and, with `clear`, one after.
+// Add the 32 copies of every half digit to the global 32-bit digits: digit
+// k takes half digits 2k and 2k + 1 (the latter shifted up 16 bits) in one
+// atomic; with `clear`, zero the copies for the next spill interval.  Needs
+// a __syncthreads() before (deposits done) and, with `clear`, one after.
 __device__ __forceinline__ void half_to_global(uint32_t* sacc, unsigned long long* gacc, bool clear) {
-  for (int h = threadIdx.x; h < kNHalf; h += blockDim.x) {
-    long long s = 0;
+  for (int k = threadIdx.x; k < kNDig; k += blockDim.x) {
+    long long s0 = 0, s1 = 0;
 #pragma unroll 8
     for (int c = 0; c < 32; c++) {
-      uint32_t* at = sacc + h * 32 + ((c + h) & 31);
-      s += (int32_t)*at;
-      if (clear) *at = 0u;
+      const int col = (c + k) & 31;  // staggered: the lanes of a warp read 32 different banks
+      uint32_t* at0 = sacc + (2 * k) * 32 + col;
+      uint32_t* at1 = sacc + (2 * k + 1) * 32 + col;
+      s0 += (int32_t)*at0;
+      s1 += (int32_t)*at1;
+      if (clear) {
+        *at0 = 0u;
+        *at1 = 0u;
+      }
     }
-    if (s) atomicAdd(gacc + (h >> 1), (unsigned long long)(s * ((h & 1) ? 65536ll : 1ll)));
+    const long long v = s0 + s1 * 65536ll;  // |v| < 2^53
+    if (v) atomicAdd(gacc + k, (unsigned long long)v);
   }
   __threadfence();
 }
@@ -287,10 +294,10 @@ template <int BLOCK, bool ALIGNED>
 __global__ void __launch_bounds__(BLOCK) k_dot_exact(int64_t n, const double* __restrict__ a,
                                                      const double* __restrict__ b, DotScratch* ws, double* out) {
   static_assert(BLOCK == 256, "the spill bound assumes 8 threads per lane copy");
-  __shared__ uint32_t sacc[kNHalf * 32];
+  __shared__ __align__(16) uint32_t sacc[kNHalf * 32];
   __shared__ long long sdig[kNDig];
   __shared__ uint32_t sD[kNDig];
-  for (int k = threadIdx.x; k < kNHalf * 32; k += BLOCK) sacc[k] = 0u;
+  for (int k = threadIdx.x; k < kNHalf * 8; k += BLOCK) reinterpret_cast<uint4*>(sacc)[k] = make_uint4(0u, 0u, 0u, 0u);
   __syncthreads();
   Window win, lo;
   window_init(win);
