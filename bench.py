@@ -95,10 +95,12 @@ def workload(side, stencil=27, band=0, band_n=0):
     return A, xt
 
 
-# DRAM traffic of one pass-A launch over its algorithmic bytes, from the ncu
-# capture summarised in profiles/k_pass_a_p27_128.md (dram read + write of the
-# 128^3 case / its algorithmic bytes); the kernel streams every matrix entry
-# once, so the full-size launch's traffic is this ratio times its bytes.
+# DRAM traffic of one pass-A launch (dram__bytes_read.sum + write.sum), from
+# the ncu captures summarised in profiles/k_pass_a_p27_128.md: the 27-point
+# 256^3 launch measured at full size (a one-pass metric), and for other
+# 27-point sizes the 128^3 launch's ratio to its algorithmic bytes (the
+# kernel streams every matrix entry once).
+PASS_A_TRAFFIC_256 = 5613844480 + 112287488
 PASS_A_TRAFFIC_RATIO = 702.0 / 710.9
 
 
@@ -423,9 +425,11 @@ def gpu_arm(args, rank, world, local_rank):
         peak, peak_kind = hbm_peak()
         ach = pass_a_bytes(n, nnz) / (a_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": (PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz)
-                            if (not args.band and args.stencil == 27) else None),
-                "traffic_source": "ncu dram bytes of the 27-point 128^3 launch scaled by algorithmic bytes",
+                "traffic": (None if (args.band or args.stencil != 27) else
+                            PASS_A_TRAFFIC_256 if args.side == 256 else PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz)),
+                "traffic_source": ("ncu dram bytes of the 27-point 256^3 pass A launch, measured at full size"
+                                   if args.side == 256 else
+                                   "ncu dram bytes of the 27-point 128^3 launch scaled by algorithmic bytes"),
                 "kernel": "k_pass_a (SpMV + <d,w> exact deposit)",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": pass_a_bytes(n, nnz), "avg_launch_ms": a_ms}
