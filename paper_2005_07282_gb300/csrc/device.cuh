@@ -438,21 +438,6 @@ __device__ __forceinline__ void two_sum(double a, double b, double& r, double& s
   s = __dadd_rn(__dsub_rn(a, __dsub_rn(r, z)), __dsub_rn(b, z));
 }
 
-// Alg. 1's result with half the FP64 work: order the operands by magnitude
-// with an integer compare of their bit patterns, then Dekker's Fast2Sum
-// (r = RN(a + b), z = RN(r - a), s = RN(b - z) is exact when |a| >= |b|).
-// The pair (r, s) of an error-free addition is unique, so this gives the
-// same values as Alg. 1.
-__device__ __forceinline__ void two_sum_ordered(double a, double b, double& r, double& s) {
-  const unsigned long long ua = (unsigned long long)__double_as_longlong(a) & 0x7FFFFFFFFFFFFFFFull;
-  const unsigned long long ub = (unsigned long long)__double_as_longlong(b) & 0x7FFFFFFFFFFFFFFFull;
-  const bool sw = ub > ua;
-  const double big = sw ? b : a, small = sw ? a : b;
-  r = __dadd_rn(big, small);
-  const double z = __dsub_rn(r, big);
-  s = __dsub_rn(small, z);
-}
-
 // Binary64 bits (sign clear) of m * 2^lsb, for m < 2^56 exactly representable
 // at or above 2^-1074 and lsb >= -1074: normalise m to 53 bits (right
 // shifts drop only zero bits), or stop at 2^-1074 (subnormal).  Adding the
@@ -768,8 +753,6 @@ __device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[
   }
   return lost;
 }
-
-constexpr double kTwoProdSafe = 0x1p-969;  // |a*b| >= this: twoprod's error term is exact
 
 // Alg. 4 from term 1 on, for a carry that term 0 has already produced.
 // A lane whose carry became zero does nothing more (the early exit); the
