@@ -723,12 +723,17 @@ __device__ __forceinline__ void fpe_level(double& fi, double& x, bool& ovf) {
   x = s;
 }
 
+// The helpers below take expansions as arrays of N terms (N = kFpeMax, or
+// fewer in kernel instances built for small p), of which the first p are in
+// use.
+
 // Alg. 4 with the early exit of Sec. 4.2; returns the value carried out of
 // the last of the p terms (0 when nothing was lost).  ovf is set if a term
 // overflows.
-__device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, double x, bool& ovf) {
+template <int N>
+__device__ __forceinline__ double fpe_accumulate(double (&f)[N], int p, double x, bool& ovf) {
 #pragma unroll
-  for (int i = 0; i < kFpeMax; i++) {
+  for (int i = 0; i < N; i++) {
     if (i < p) {
       fpe_level(f[i], x, ovf);
       if (is_zero_bits(x)) break;
@@ -741,13 +746,14 @@ __device__ __forceinline__ double fpe_accumulate(double (&f)[kFpeMax], int p, do
 // The loop over b's terms is rolled (the term is picked by selects, so both
 // expansions stay in registers): one copy of Alg. 4's loop instead of
 // kFpeMax keeps the code small.
-__device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[kFpeMax], int p, bool& ovf) {
+template <int N>
+__device__ __forceinline__ bool fpe_sum(double (&a)[N], const double (&b)[N], int p, bool& ovf) {
   bool lost = false;
 #pragma unroll 1
   for (int i = 0; i < p; i++) {
     double bi = b[0];
 #pragma unroll
-    for (int k = 1; k < kFpeMax; k++)
+    for (int k = 1; k < N; k++)
       if (i == k) bi = b[k];
     if (!is_zero_bits(bi)) lost |= !is_zero_bits(fpe_accumulate(a, p, bi, ovf));
   }
@@ -759,11 +765,11 @@ __device__ __forceinline__ bool fpe_sum(double (&a)[kFpeMax], const double (&b)[
 // warp leaves the unrolled levels as soon as no lane here has a carry left.
 // That exit is a vote, so the branch is the same in every lane and stays a
 // branch: with per-lane exits alone the levels ran as predicated code, and
-// every element issued the FP64 additions of all kFpeMax - 1 levels.
-template <bool FAST = false>
-__device__ __forceinline__ double fpe_accumulate_from1(double (&f)[kFpeMax], int p, double x, bool& ovf) {
+// every element issued the FP64 additions of all N - 1 levels.
+template <bool FAST, int N>
+__device__ __forceinline__ double fpe_accumulate_from1(double (&f)[N], int p, double x, bool& ovf) {
 #pragma unroll
-  for (int i = 1; i < kFpeMax; i++) {
+  for (int i = 1; i < N; i++) {
     if (i < p) {
       if (__all_sync(__activemask(), is_zero_bits(x))) break;
       if (!is_zero_bits(x)) fpe_level<FAST>(f[i], x, ovf);
@@ -793,7 +799,8 @@ constexpr bool kFpeErrFast = false;
 // so a zero error term changes nothing).  A product or a term that
 // overflows sets `nonfinite` (the dot's value is then NaN, as the FP64
 // formulas' non-finite terms would make it).
-__device__ __forceinline__ bool fpe_dot_step(double (&res)[kFpeMax], double (&err)[kFpeMax], int p, double a, double b,
+template <int N>
+__device__ __forceinline__ bool fpe_dot_step(double (&res)[N], double (&err)[N], int p, double a, double b,
                                              bool& nonfinite) {
   if (is_zero_bits(a) || is_zero_bits(b)) return false;  // adds nothing
   double r, s;
