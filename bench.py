@@ -104,6 +104,18 @@ PASS_A_TRAFFIC_256 = 5613844480 + 112287488
 PASS_A_TRAFFIC_RATIO = 702.0 / 710.9
 
 
+def pass_a_traffic(args, n, nnz):
+    """(bytes, source) of one pass-A launch's DRAM traffic for the roofline
+    record: measured at 27-point 256^3, scaled from 128^3 for other 27-point
+    sizes, None for workloads no capture covers."""
+    if args.band or args.stencil != 27:
+        return None, None
+    if args.side == 256:
+        return PASS_A_TRAFFIC_256, "ncu dram bytes of the 27-point 256^3 pass A launch, measured at full size"
+    return (PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz),
+            "ncu dram bytes of the 27-point 128^3 launch scaled by algorithmic bytes")
+
+
 # Pipe utilisation of the fpe variant's three FPE-dot kernels, from the ncu
 # full-set capture summarised in profiles/k_fpe_dots_p27_128.md (27-point
 # 128^3, percent of each pipe's own peak while the SMs are active).  The
@@ -425,11 +437,8 @@ def gpu_arm(args, rank, world, local_rank):
         peak, peak_kind = hbm_peak()
         ach = pass_a_bytes(n, nnz) / (a_ms * 1e-3) / 1e9
         roof = {"bound": "hbm", "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
-                "traffic": (None if (args.band or args.stencil != 27) else
-                            PASS_A_TRAFFIC_256 if args.side == 256 else PASS_A_TRAFFIC_RATIO * pass_a_bytes(n, nnz)),
-                "traffic_source": ("ncu dram bytes of the 27-point 256^3 pass A launch, measured at full size"
-                                   if args.side == 256 else
-                                   "ncu dram bytes of the 27-point 128^3 launch scaled by algorithmic bytes"),
+                "traffic": pass_a_traffic(args, n, nnz)[0],
+                "traffic_source": pass_a_traffic(args, n, nnz)[1],
                 "kernel": "k_pass_a (SpMV + <d,w> exact deposit)",
                 "peak_kind": f"{peak_kind} copy bandwidth",
                 "algorithmic_bytes_per_launch": pass_a_bytes(n, nnz), "avg_launch_ms": a_ms}

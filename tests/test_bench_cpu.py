@@ -59,3 +59,27 @@ def test_reference_arm_json_line():
     assert line["config"]["workload"] == "poisson7_6 exblas"
     # the same workload record as the GPU arm's line (the driver compares the two arms)
     assert line["config"] == bench.workload_config(A, line["config"]["n"], line["config"]["nnz"])
+
+
+def test_pass_a_traffic_record():
+    """The roofline record's DRAM traffic: the full-size capture at 27-point
+    256^3 (within 0.1% of the algorithmic bytes: every entry and vector
+    element crosses HBM once), the 128^3 ratio at other 27-point sizes, and
+    no figure where no capture applies."""
+    import bench
+
+    class A:
+        band, stencil, side = 0, 27, 256
+
+    n, nnz = 256 ** 3, (3 * 256 - 2) ** 3
+    t, src = bench.pass_a_traffic(A, n, nnz)
+    assert t == 5_726_131_968 and "256^3" in src and "full size" in src
+    assert abs(t / bench.pass_a_bytes(n, nnz) - 1.0) < 1e-3
+    A.side = 128
+    n, nnz = 128 ** 3, (3 * 128 - 2) ** 3
+    t, src = bench.pass_a_traffic(A, n, nnz)
+    assert "128^3" in src and abs(t / bench.pass_a_bytes(n, nnz) - 702.0 / 710.9) < 1e-12
+    A.stencil = 7
+    assert bench.pass_a_traffic(A, n, nnz) == (None, None)
+    A.stencil, A.band = 27, 100
+    assert bench.pass_a_traffic(A, n, nnz) == (None, None)
