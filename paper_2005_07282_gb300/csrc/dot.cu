@@ -145,23 +145,16 @@ __device__ __forceinline__ void window_chain(Window& w, uint32_t m, uint32_t a0,
       : "r"(m), "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(a4), "r"(a5));
 }
 
-// W += the signed product at word offset t1 (0 or 1) in the window.  BR
-// picks the form: a branch to the chain with the words already in place,
-// which runs one chain when the lanes of the warp agree on t1 (products that
-// span a few bits of exponent share their digit index), or six selects,
-// which cost less than running both chains when they do not.  The main
-// window takes the branch (on U[-1, 1] pairs 7% faster than selects), the
-// low window, which only data with a wide exponent spread reaches, the
-// selects (on pairs of condition 1e32 the branch there was 6% slower).
-template <bool BR>
+// W += the signed product at word offset t1 (0 or 1) in the window, the
+// words placed by six selects.  The main window instead branches on the
+// offset (half_exact_deposit): when the lanes of a warp agree on it, as
+// products that span a few bits of exponent do, one chain runs with the
+// words already in place (on U[-1, 1] pairs 7% faster than selects); the
+// low window, which only data with a wide exponent spread reaches, keeps
+// the selects (a branch there was 6% slower on pairs of condition 1e32).
 __device__ __forceinline__ void window_add_c(Window& w, const WinProd& p, bool t1) {
-  if constexpr (BR) {
-    if (t1) window_chain(w, p.m, p.m, p.w0, p.w1, p.w2, p.w3, p.w4);
-    else window_chain(w, p.m, p.w0, p.w1, p.w2, p.w3, p.w4, p.m);
-  } else {
-    window_chain(w, p.m, t1 ? p.m : p.w0, t1 ? p.w0 : p.w1, t1 ? p.w1 : p.w2, t1 ? p.w2 : p.w3,
-                 t1 ? p.w3 : p.w4, t1 ? p.w4 : p.m);
-  }
+  window_chain(w, p.m, t1 ? p.m : p.w0, t1 ? p.w0 : p.w1, t1 ? p.w1 : p.w2, t1 ? p.w2 : p.w3, t1 ? p.w3 : p.w4,
+               t1 ? p.w4 : p.m);
 }
 
 // A product that no register window takes: the ten 16-bit chunks of its
@@ -215,10 +208,12 @@ __device__ __forceinline__ void half_exact_deposit(Window& w, Window& lo, uint32
                                                    const WinProd& p) {
   if (!p.nz) return;
   const int t = p.q - w.qb;
-  if ((unsigned)t < 2u) {
-    window_add_c<true>(w, p, t == 1);
+  if (t == 1) {  // the main window by branch, the common offset first
+    window_chain(w, p.m, p.m, p.w0, p.w1, p.w2, p.w3, p.w4);
+  } else if (t == 0) {
+    window_chain(w, p.m, p.w0, p.w1, p.w2, p.w3, p.w4, p.m);
   } else if ((unsigned)(t + 2) < 2u) {
-    window_add_c<false>(lo, p, t == -1);
+    window_add_c(lo, p, t == -1);
   } else {
     half_deposit(sacc, p);
     if (t > 1) qtop = max(qtop, p.q);
